@@ -1,0 +1,225 @@
+/*
+ * qaoa.h - C ABI of the GB300 (sm_103a) statevector library for depth-p QAOA
+ * on random NAE-k-SAT (arXiv 2401.02852).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Assignment index x = sum_l x_l 2^l: variable l is bit l of x.  X_j flips
+ *    bit j.  (The paper's decimal representation in Appendix A.3 is garbled;
+ *    this is the reading used throughout.)
+ *  - A literal (v, neg) takes the value of bit v of x, complemented when
+ *    neg = 1 (negated literal, Eq. for the literal Hamiltonian, Appendix A.2).
+ *  - State vectors are device arrays of 2^n complex amplitudes, interleaved
+ *    (re, im): QAOA_C64 = 2 x float (8 bytes), QAOA_C128 = 2 x double (16 bytes).
+ *  - Cost tables are device uint8 arrays of 2^n entries, C(x) exact.
+ *  - Angles are host float64 arrays in radians; layer 0 (gamma[0], beta[0])
+ *    acts first on |+>^n (the product of the QAOA output state, Sec. "QAOA
+ *    Procedure", read right to left).
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Device pointers are owned by the caller; the library never frees them.
+ *    The library keeps its own small per-(device, stream) scratch (reduction
+ *    partials, counters, pinned result slots), allocated on first use on that
+ *    stream and released by qaoa_release_scratch().
+ *  - Host result pointers (p_succ, norm, n_sol, ...) are written before the
+ *    call returns: such calls synchronise the stream.  Passing NULL skips the
+ *    result (and the reduction that produces it) where documented.
+ *  - Every entry point returns an int status (QAOA_OK = 0, QAOA_PENDING > 0,
+ *    errors < 0); no exception crosses the ABI.  qaoa_last_error() gives a
+ *    thread-local message for the last failing call of the calling thread.
+ *  - Arguments are validated on the host before any device work; an invalid
+ *    call changes no device memory.
+ */
+#ifndef QAOA_NAESAT_H
+#define QAOA_NAESAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QAOA_OK 0
+#define QAOA_PENDING 1     /* serving: request not finished yet                */
+#define QAOA_EINVAL (-1)   /* malformed argument (NULL, bad enum, bad clause)   */
+#define QAOA_ERANGE (-2)   /* size out of range (n > 32, m > 1023, k > n,
+                              max C > 255 for the uint8 table, tile limits)     */
+#define QAOA_ENOMEM (-3)   /* device or host allocation failed / over budget    */
+#define QAOA_ECUDA (-4)    /* a CUDA runtime call failed (message has details)  */
+#define QAOA_ETIMEOUT (-5) /* serving: wait deadline passed                     */
+#define QAOA_ECANCELLED (-6) /* serving: request cancelled                      */
+#define QAOA_ENOTFOUND (-7)  /* serving: unknown ticket                         */
+
+/* ---- element types and flags ------------------------------------------- */
+#define QAOA_C64 0  /* complex64 state, FP32 butterflies, FP64 reductions   */
+#define QAOA_C128 1 /* complex128 state, FP64 throughout                    */
+
+/* Mixer sign.  The paper writes U_B(beta) = exp(-i beta H_B) in Sec. 2.1 but
+ * uses U_B(beta) = exp(+i beta sum_j X_j) = prod_j [cos(beta) I + i sin(beta)
+ * X_j] for the NAE problem (Sec. "Efficient Classical Simulation", Appendix
+ * A.3, "due to the problem being recast as a minimisation").  The default is
+ * the latter.  QAOA_MIXER_RX2B selects exp(-i beta sum_j X_j) = prod_j RX(2 beta). */
+#define QAOA_MIXER_PAPER 0x0
+#define QAOA_MIXER_RX2B 0x1
+
+#define QAOA_MAX_N 32
+#define QAOA_MAX_M 1023
+
+/* One NAE-k-SAT instance, host memory.  var[i*k + j] in [0, n) is the variable
+ * of literal j of clause i (distinct within a clause); neg[i*k + j] in {0, 1}
+ * marks a negated literal.  Sec. "Random Problems" / Def. of CNF(n, k, r). */
+typedef struct {
+    int32_t n, m, k;
+    const int32_t *var;
+    const uint8_t *neg;
+} naesat_instance;
+
+/* Thread-local text of the last error of the calling thread ("" if none). */
+const char *qaoa_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int qaoa_version(void);
+
+/* Releases the library's scratch on every device (call with no work in
+ * flight).  Returns QAOA_OK. */
+int qaoa_release_scratch(void);
+
+/* ---- cost table (Eq. for C^NAE, Sec. "Problem Hamiltonian") ----------------
+ * C(x) = number of clauses whose k literals are all false or all true
+ * (De Morgan form, Appendix A.2), for every x in [0, 2^n).
+ *   inst      host instance (validated: 1 <= n <= 32, 0 <= m <= 1023,
+ *             1 <= k <= n, variables distinct within a clause).
+ *   d_cost    device uint8 [2^n], written.
+ *   n_sol     host, nullable: number of x with C(x) = 0 (exact brute force).
+ *   max_cost  host, nullable: max_x C(x).
+ * Returns QAOA_ERANGE (and leaves d_cost with every entry taken mod 256) when
+ * some C(x) > 255; n_sol and max_cost are still exact in that case.
+ * Synchronises the stream when n_sol or max_cost is requested. */
+int naesat_cost_table(const naesat_instance *inst, uint8_t *d_cost, uint64_t *n_sol,
+                      uint32_t *max_cost, void *stream);
+
+/* Same for `batch` instances of one n: d_costs is device uint8 [batch][2^n];
+ * n_sol / max_cost are host arrays [batch] (nullable). */
+int naesat_cost_table_batch(int batch, const naesat_instance *insts, uint8_t *d_costs,
+                            uint64_t *n_sol, uint32_t *max_cost, void *stream);
+
+/* ---- state evolution (Eq. for the QAOA output state) -----------------------
+ * d_state <- prod_{l=0}^{p-1} U_B(beta_l) U_C(gamma_l) |+>^n, with
+ * U_C(gamma) = diag(exp(-i gamma C(x))) (Eq. for U_C) and the mixer of `flags`.
+ *   n        1..32 (C64) / 1..31 (C128); the state must fit in device memory.
+ *   d_cost   device uint8 [2^n] from naesat_cost_table.
+ *   m        number of clauses (bounds C; phase tables have m + 1 entries).
+ *   p        depth >= 0 (p = 0 returns |+>^n).
+ *   gamma, beta  host float64 [p].
+ *   dtype    QAOA_C64 or QAOA_C128.
+ *   d_state  device [2^n] of dtype, written (no input is read from it).
+ *   p_succ, norm  host, nullable: p_succ = sum_{C(x)=0} |psi(x)|^2 (Def. of the
+ *            success probability, unnormalised) and sum_x |psi(x)|^2, reduced
+ *            in FP64 inside the last pass.
+ * Synchronises the stream when p_succ or norm is requested. */
+int qaoa_evolve(int n, const uint8_t *d_cost, int m, int p, const double *gamma, const double *beta,
+                int dtype, int flags, void *d_state, double *p_succ, double *norm, void *stream);
+
+/* `batch` independent instances of one n sharing the angles:
+ * d_costs [batch][2^n], d_states [batch][2^n], m_max = max clause count,
+ * p_succ / norm host [batch] (nullable). */
+int qaoa_evolve_batch(int batch, int n, const uint8_t *d_costs, int m_max, int p, const double *gamma,
+                      const double *beta, int dtype, int flags, void *d_states, double *p_succ,
+                      double *norm, void *stream);
+
+/* ---- success probability (Def. of the k-NAE-SAT success probability) -------
+ * p_succ = sum_{x: C(x)=0} |psi(x)|^2 and norm = sum_x |psi(x)|^2 of a given
+ * device state (FP64 accumulation, deterministic order).  Both host outputs
+ * are required.  Synchronises the stream. */
+int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_state, int dtype, double *p_succ,
+                      double *norm, void *stream);
+
+/* ---- gradient ----------------------------------------------------------------
+ * dp_succ/dgamma_l and dp_succ/dbeta_l by a reverse sweep that recomputes the
+ * states backward with inverse layers (no stored intermediate states).  The
+ * paper trains the fixed angles by gradient ascent on p_succ (Sec. "QAOA
+ * Procedure"); this is the adjoint form of that derivative.
+ *   d_state, d_adj  device scratch [2^n] of dtype each (overwritten; on
+ *            return d_state holds |+>^n up to rounding, d_adj the adjoint).
+ *   p_succ   host, nullable; dgamma, dbeta host float64 [p], written.
+ * Synchronises the stream. */
+int qaoa_grad(int n, const uint8_t *d_cost, int m, int p, const double *gamma, const double *beta,
+              int dtype, int flags, void *d_state, void *d_adj, double *p_succ, double *dgamma,
+              double *dbeta, void *stream);
+
+/* Batched gradient for `batch` instances of one n sharing the angles.
+ * d_costs [batch][2^n]; d_states, d_adjs [batch][2^n] scratch;
+ * p_succ host [batch] (nullable); dgamma, dbeta host [batch][p]. */
+int qaoa_grad_batch(int batch, int n, const uint8_t *d_costs, int m_max, int p, const double *gamma,
+                    const double *beta, int dtype, int flags, void *d_states, void *d_adjs,
+                    double *p_succ, double *dgamma, double *dbeta, void *stream);
+
+/* ---- serving: continuous batching of whole requests ---------------------------
+ * A server owns a scheduler thread, device memory for resident cost tables and
+ * states (bounded by hbm_budget_bytes) and a few CUDA streams.  Requests of any
+ * n (1..max_n) and depth arrive through qaoa_serve_submit; each is admitted
+ * when its footprint fits the budget and a slot is free, packed with other
+ * small-n requests into one launch when n <= small_n_max, and otherwise run as
+ * its own multi-pass evolution on one of the streams.  Results are read with
+ * qaoa_serve_poll / qaoa_serve_wait.  (Not in the paper: a serving pattern
+ * around its simulation.) */
+typedef struct qaoa_server qaoa_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* admission budget for resident tables + states (0 = 50% of free) */
+    int max_batch;           /* max requests per packed small-n launch (0 = 256)               */
+    int n_streams;           /* CUDA streams for large requests (0 = 4)                       */
+    int dtype;               /* QAOA_C64 or QAOA_C128                                          */
+    int small_n_max;         /* n at or below which requests are packed (0 = default)         */
+    int flags;               /* mixer sign flags, as for qaoa_evolve                           */
+    int device;              /* CUDA device ordinal                                            */
+    int max_n;               /* largest n accepted (0 = 30)                                    */
+} qaoa_server_opts;
+
+typedef struct {
+    double p_succ, norm;     /* as qaoa_evolve                                                 */
+    uint64_t n_sol;          /* number of x with C(x) = 0                                       */
+    uint32_t max_cost;       /* max_x C(x)                                                     */
+    int32_t status;          /* QAOA_OK, or the error of this request                          */
+    uint64_t t_submit_ns, t_start_ns, t_done_ns; /* CLOCK_MONOTONIC nanoseconds                */
+} qaoa_result;
+
+int qaoa_server_create(const qaoa_server_opts *opts, qaoa_server **out);
+/* Copies the instance and angles; returns at once with a ticket. */
+int qaoa_serve_submit(qaoa_server *s, const naesat_instance *inst, int p, const double *gamma,
+                      const double *beta, uint64_t *ticket);
+/* QAOA_OK with *out filled (the ticket is then retired), QAOA_PENDING, or an error. */
+int qaoa_serve_poll(qaoa_server *s, uint64_t ticket, qaoa_result *out);
+/* Blocks until the ticket finishes or timeout_s passes (QAOA_ETIMEOUT). */
+int qaoa_serve_wait(qaoa_server *s, uint64_t ticket, qaoa_result *out, double timeout_s);
+/* Cancels a request that has not started; QAOA_OK or QAOA_PENDING if running. */
+int qaoa_serve_cancel(qaoa_server *s, uint64_t ticket);
+/* Counters: submitted, completed, packed launches, single launches, peak bytes. */
+int qaoa_server_stats(qaoa_server *s, uint64_t *counters /* [8] */);
+/* Drains running work, joins the scheduler, frees device memory. */
+int qaoa_server_destroy(qaoa_server *s);
+
+/* ---- pass planning and instrumentation (host only, no device work) ----------
+ * qaoa_plan describes how one layer of an n-qubit evolution in dtype is split
+ * into HBM passes.  Pass 0 streams contiguous tiles and mixes qubits
+ * [0, row_bits[0]).  Pass i > 0 streams tiles of 2^row_bits[i] contiguous
+ * amplitudes times 2^G rows strided by 2^group_lo[i] (G = tile bits -
+ * row_bits[i]) and mixes the top group_bits[i] qubits of its group.  Returns
+ * the number of passes per layer (>= 1) or an error; arrays hold up to 8. */
+int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits);
+
+/* Per-kernel timing: when enabled, every kernel the library launches is
+ * bracketed by CUDA events on its stream.  qaoa_profile_read synchronises the
+ * device, then returns for kernel kind i (names via qaoa_kernel_name) the
+ * launch count and summed milliseconds; it resets the accumulators. */
+int qaoa_profile_enable(int on);
+int qaoa_profile_read(int max_kinds, uint64_t *launches, double *ms);
+const char *qaoa_kernel_name(int kind);
+/* Total kernels launched by this library in this process. */
+uint64_t qaoa_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QAOA_NAESAT_H */

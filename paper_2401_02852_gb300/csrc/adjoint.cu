@@ -1,0 +1,458 @@
+// K5: gradient of p_succ with respect to the angles by a reverse (adjoint)
+// sweep that recomputes the states backward with inverse layers.
+//
+// Forward: phi_l = D_l psi_{l-1}, psi_l = M_l phi_l, D_l = exp(-i gamma_l C),
+// M_l = exp(i s beta_l B), B = sum_j X_j, f = <psi_p| P |psi_p>, P the
+// projector on C = 0 (Def. of the success probability).  With
+// lam_p = P psi_p and, going backward,
+//   df/dbeta_l  = 2 Re <lam_l| i s B |psi_l> = -2 s Im <lam_l| B |psi_l>,
+//   (phi_l, mu_l) = M_l^dagger (psi_l, lam_l),
+//   df/dgamma_l = 2 Re <mu_l| -i C |phi_l> = 2 sum_x C(x) Im(conj(mu_x) phi_x),
+//   (psi_{l-1}, lam_{l-1}) = D_l^dagger (phi_l, mu_l).
+// Every X_j commutes with every single-qubit factor of M_l, so the term of qubit
+// j, Im(conj(a') b + conj(b') a) over the pairs (x, x xor 2^j), is taken at the
+// moment qubit j's inverse butterfly runs; the inverse butterflies are the
+// normalised ones (c a - i S b, c b - i S a), so the states stay unit-norm.
+//
+// The paper differentiates through its simulator with automatic
+// differentiation (Sec. "QAOA Procedure", training of the fixed angles); this
+// computes the same derivative without storing the p intermediate states.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "pass_common.cuh"
+#include "qaoa_internal.cuh"
+
+namespace qaoa {
+
+template <typename R>
+using AGeo = Geo<R, 12, 4>;  // 2 tiles (psi, lam) of 2^12 amplitudes
+
+template <typename R>
+struct AdjArgs {
+    typename AGeo<R>::V *psi, *lam;
+    const uint8_t *cost;
+    double *partials;  // this layer's slice: [batch][p][gx][2], base at layer l
+    int n, row, lo, m, p;
+    uint32_t active;
+    R c, S;            // inverse butterfly coefficients
+    uint64_t tiles;
+};
+
+template <typename R, int NT>
+struct AdjTab {
+    typename AGeo<R>::V t[NT];  // exp(+i gamma c)
+};
+
+// Inverse butterfly on psi and lam for the pair (i, j), with the mixer term.
+template <typename V, typename R>
+__device__ __forceinline__ void inv_pair(V &a, V &b, V &la, V &lb, R c, R S, R &term) {
+    term += la.x * b.y - la.y * b.x + lb.x * a.y - lb.y * a.x;
+    V na, nb;
+    na.x = fma(c, a.x, S * b.y);
+    na.y = fma(c, a.y, -S * b.x);
+    nb.x = fma(c, b.x, S * a.y);
+    nb.y = fma(c, b.y, -S * a.x);
+    a = na;
+    b = nb;
+    na.x = fma(c, la.x, S * lb.y);
+    na.y = fma(c, la.y, -S * lb.x);
+    nb.x = fma(c, lb.x, S * la.y);
+    nb.y = fma(c, lb.y, -S * la.x);
+    la = na;
+    lb = nb;
+}
+
+template <typename G, int LO, int BELOW>
+__device__ __forceinline__ void inv_round(typename G::V *vp, typename G::V *vl, uint32_t mask, typename G::Real c,
+                                          typename G::Real S, typename G::Real &term) {
+    constexpr int RB = G::RB, NR = G::NR;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+        if (LO + q < BELOW && ((mask >> (LO + q)) & 1u)) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i)
+                if (!(i & (1 << q))) inv_pair(vp[i], vp[i | (1 << q)], vl[i], vl[i | (1 << q)], c, S, term);
+        }
+    }
+}
+
+template <typename R, bool LOW, int NT>
+__global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const __grid_constant__ AdjArgs<R> a,
+                                                                        const __grid_constant__ AdjTab<R, NT> tab) {
+    using G = AGeo<R>;
+    using V = typename G::V;
+    constexpr int T = G::T, NR = G::NR;
+    constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tp = reinterpret_cast<V *>(smem_raw);
+    V *tl = tp + (1 << T);
+    V *stab = tl + (1 << T);
+    if (LOW) {  // 256 entries at least: any uint8 cost indexes inside the table
+        for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
+            V z;
+            z.x = z.y = 0;
+            stab[i] = i <= a.m ? tab.t[i] : z;
+        }
+        __syncthreads();
+    }
+    const uint32_t tid = threadIdx.x;
+    const size_t inst = blockIdx.y;
+    V *psi = a.psi + (inst << a.n);
+    V *lam = a.lam + (inst << a.n);
+    const uint8_t *cs = a.cost + (inst << a.n);
+    const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<G, 8>(tid, 0), a.row, a.lo);
+    const uint64_t ld_s = LOW ? 256u : (1ull << (a.lo + 8 - a.row));
+    const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
+    const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
+    double acc[2] = {0.0, 0.0};  // mixer term, phase term
+    for (uint64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+        const uint64_t base = tile_base(t, a.row, a.lo, T);
+        V vp[NR], vl[NR];
+        {
+            const V *pp = psi + base + ld_t;
+            const V *pl = lam + base + ld_t;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                vp[r] = pp[r * ld_s];
+                vl[r] = pl[r * ld_s];
+            }
+        }
+        R term = 0;
+        inv_round<G, 8, T>(vp, vl, a.active, a.c, a.S, term);
+        if (LOW) {
+            exchange<G, 8, 0>(vp, tp);
+            exchange<G, 8, 0>(vl, tl);
+            inv_round<G, 0, T>(vp, vl, a.active, a.c, a.S, term);
+            exchange<G, 0, LC>(vp, tp);
+            exchange<G, 0, LC>(vl, tl);
+        } else {
+            exchange<G, 8, LC>(vp, tp);
+            exchange<G, 8, LC>(vl, tl);
+        }
+        inv_round<G, LC, 8>(vp, vl, a.active, a.c, a.S, term);
+        R gterm = 0;
+        {
+            V *pp = psi + base + st_t;
+            asm volatile("" : "+l"(pp));  // keep the store addresses out of the load phase
+            V *pl = lam + base + st_t;
+            const uint8_t *pc = cs + base + st_t;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (LOW) {  // all of M_l undone: phase term, then D_l^dagger
+                    const int cst = pc[r * st_s];
+                    gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
+                    const V ph = stab[cst];
+                    vp[r] = cmul(vp[r], ph);
+                    vl[r] = cmul(vl[r], ph);
+                }
+                pp[r * st_s] = vp[r];
+                pl[r * st_s] = vl[r];
+            }
+        }
+        acc[0] += (double)term;
+        acc[1] += (double)gterm;
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        double *out = a.partials + 2 * ((inst * a.p) * gridDim.x + blockIdx.x);
+        out[0] += acc[0];
+        out[1] += acc[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small n: the whole forward and reverse sweep of one instance per CTA, both
+// states resident in shared memory.  tables: FP64 exp(-i gamma_l c) [p][m+1];
+// coefs: (c, S) per layer.  out: [batch][1 + p][2] = (p_succ, norm), then
+// (mixer sum, phase sum) per layer.
+template <typename R>
+__global__ void __launch_bounds__(PT) small_grad_kernel(const uint8_t *costs, int n, int m, int p, const double *tables,
+                                                        const double *coefs, double *out) {
+    using V = typename Cx<R>::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t N = 1u << n;
+    V *sp = reinterpret_cast<V *>(smem_raw);
+    V *sl = sp + N;
+    uint8_t *sc = reinterpret_cast<uint8_t *>(sl + N);
+    const size_t inst = blockIdx.x;
+    const uint8_t *cost = costs + (inst << n);
+    double *o = out + inst * 2 * (1 + p);
+    for (uint32_t x = threadIdx.x; x < N; x += PT) sc[x] = cost[x];
+    const R amp = (R)(1.0 / sqrt((double)N));
+    for (uint32_t x = threadIdx.x; x < N; x += PT) sp[x] = V{amp, (R)0};
+    __syncthreads();
+    for (int l = 0; l < p; ++l) {
+        const double *tb = tables + 2 * (size_t)l * (m + 1);
+        for (uint32_t x = threadIdx.x; x < N; x += PT) {
+            const int cx = min((int)sc[x], m);
+            const V ph{(R)tb[2 * cx], (R)tb[2 * cx + 1]};
+            sp[x] = cmul(sp[x], ph);
+        }
+        const R c = (R)coefs[2 * l], S = (R)coefs[2 * l + 1];
+        for (int j = 0; j < n; ++j) {
+            __syncthreads();
+            for (uint32_t g = threadIdx.x; g < N / 2; g += PT) {
+                const uint32_t x0 = ((g >> j) << (j + 1)) | (g & ((1u << j) - 1u)), x1 = x0 | (1u << j);
+                const V a = sp[x0], b = sp[x1];
+                sp[x0] = V{fma(c, a.x, -S * b.y), fma(c, a.y, S * b.x)};
+                sp[x1] = V{fma(c, b.x, -S * a.y), fma(c, b.y, S * a.x)};
+            }
+        }
+        __syncthreads();
+    }
+    double acc[2] = {0.0, 0.0};
+    for (uint32_t x = threadIdx.x; x < N; x += PT) {
+        const V v = sp[x];
+        const double w = (double)v.x * v.x + (double)v.y * v.y;
+        acc[1] += w;
+        const bool sol = sc[x] == 0;
+        if (sol) acc[0] += w;
+        sl[x] = sol ? v : V{(R)0, (R)0};
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        o[0] = acc[0];
+        o[1] = acc[1];
+    }
+    for (int l = p - 1; l >= 0; --l) {
+        const R c = (R)coefs[2 * l], S = (R)coefs[2 * l + 1];
+        R term = 0;
+        for (int j = 0; j < n; ++j) {
+            __syncthreads();
+            for (uint32_t g = threadIdx.x; g < N / 2; g += PT) {
+                const uint32_t x0 = ((g >> j) << (j + 1)) | (g & ((1u << j) - 1u)), x1 = x0 | (1u << j);
+                V a = sp[x0], b = sp[x1], la = sl[x0], lb = sl[x1];
+                inv_pair(a, b, la, lb, c, S, term);
+                sp[x0] = a;
+                sp[x1] = b;
+                sl[x0] = la;
+                sl[x1] = lb;
+            }
+        }
+        __syncthreads();
+        const double *tb = tables + 2 * (size_t)l * (m + 1);
+        R gterm = 0;
+        for (uint32_t x = threadIdx.x; x < N; x += PT) {
+            const int cst = min((int)sc[x], m);
+            const V vp = sp[x], vl = sl[x];
+            gterm += (R)cst * (vl.x * vp.y - vl.y * vp.x);
+            const V ph{(R)tb[2 * cst], (R)(-tb[2 * cst + 1])};
+            sp[x] = cmul(vp, ph);
+            sl[x] = cmul(vl, ph);
+        }
+        double g2[2] = {(double)term, (double)gterm};
+        block_sum<2>(g2);
+        if (threadIdx.x == 0) {
+            o[2 * (1 + l)] = g2[0];
+            o[2 * (1 + l) + 1] = g2[1];
+        }
+    }
+}
+
+template <typename R>
+static size_t adj_smem(int m) {
+    return sizeof(typename AGeo<R>::V) * (2 * (size_t(1) << AGeo<R>::T) + (m < 0 ? 0 : (size_t)(m < 255 ? 256 : m + 1)));
+}
+
+template <typename R>
+static int adj_init() {
+    static std::mutex mu;
+    static int state = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (state == 0) {
+        const int big = (int)adj_smem<R>(QAOA_MAX_M);
+        cudaError_t e = cudaFuncSetAttribute(adj_kernel<R, true, MAX_TABLE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(adj_kernel<R, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        const int small = (int)(2 * sizeof(typename Cx<R>::V) * (size_t(1) << Cx<R>::T) + (size_t(1) << Cx<R>::T));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(small_grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
+        state = e == cudaSuccess ? 1 : -1;
+        if (e != cudaSuccess) return cuda_error(e, "adjoint kernel attributes");
+    }
+    return state > 0 ? QAOA_OK : set_error(QAOA_ECUDA, "adjoint kernels unavailable");
+}
+
+template <typename R>
+static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, const double *gamma, const double *beta,
+                       int dtype, int flags, void *state, void *adj, double *d_scr, double *h_scr,
+                       cudaStream_t stream, double *p_succ, double *dgamma, double *dbeta) {
+    using V = typename AGeo<R>::V;
+    int rc = adj_init<R>();
+    if (rc) return rc;
+    const int sign = (flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    // forward with the adjoint seed lam_p = P psi_p written by the last pass
+    const int gxf = pass_grid_x(dtype, n, batch);
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    int gxa = (int)(((uint64_t)di.sms * (sizeof(R) == 4 ? 2 : 1) + batch - 1) / batch);
+    const uint64_t tiles = 1ull << (n - AGeo<R>::T);
+    if (gxa < 1) gxa = 1;
+    if ((uint64_t)gxa > tiles) gxa = (int)tiles;
+    double *d_fpart = d_scr;                                  // batch * gxf * 2
+    double *d_fres = d_fpart + (size_t)batch * gxf * 2;       // batch * 2
+    double *d_apart = d_fres + (size_t)batch * 2;             // batch * p * gxa * 2
+    double *d_ares = d_apart + (size_t)batch * p * gxa * 2;   // batch * p * 2
+    EvolveReq r{batch, n, m, p, dtype, flags, cost, state, adj, gamma, beta, d_fres};
+    if ((rc = evolve_device_impl(r, stream, d_fpart, gxf))) return rc;
+    QAOA_CUDA_TRY(cudaMemsetAsync(d_apart, 0, (size_t)batch * p * gxa * 2 * sizeof(double), stream));
+    Plan pl;
+    if ((rc = make_plan_geo(n, AGeo<R>::T, 8, &pl))) return rc;
+    std::vector<char> tbuf(sizeof(AdjTab<R, MAX_TABLE>));
+    auto *tab = reinterpret_cast<AdjTab<R, MAX_TABLE> *>(tbuf.data());
+    AdjTab<R, 1> none{};
+    for (int l = p - 1; l >= 0; --l) {
+        const double c = std::cos(beta[l]), S = sign * std::sin(beta[l]);
+        for (int k = 0; k <= m; ++k) {
+            tab->t[k].x = (R)std::cos(gamma[l] * k);
+            tab->t[k].y = (R)std::sin(gamma[l] * k);
+        }
+        for (int i = pl.n_passes - 1; i >= 0; --i) {
+            const Pass &ps = pl.pass[i];
+            AdjArgs<R> a;
+            a.psi = reinterpret_cast<V *>(state);
+            a.lam = reinterpret_cast<V *>(adj);
+            a.cost = cost;
+            a.partials = d_apart + (size_t)l * gxa * 2;
+            a.n = n;
+            a.m = m;
+            a.p = p;
+            a.c = (R)c;
+            a.S = (R)S;
+            a.tiles = tiles;
+            if (i == 0) {
+                a.row = AGeo<R>::T;
+                a.lo = AGeo<R>::T;
+                a.active = (1u << AGeo<R>::T) - 1u;
+                profile_before(K_ADJ_LOW, stream);
+                adj_kernel<R, true, MAX_TABLE>
+                    <<<dim3(gxa, batch), PT, adj_smem<R>(m), stream>>>(a, *tab);
+                rc = profile_after(K_ADJ_LOW, stream);
+            } else {
+                a.row = ps.row;
+                a.lo = ps.lo;
+                a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
+                profile_before(K_ADJ_HIGH, stream);
+                adj_kernel<R, false, 1><<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);
+                rc = profile_after(K_ADJ_HIGH, stream);
+            }
+            if (rc) return rc;
+        }
+    }
+    if ((rc = launch_reduce(d_apart, batch * p, gxa, 2, d_ares, stream))) return rc;
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h_scr, d_fres, (size_t)batch * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h_scr + 2 * batch, d_ares, (size_t)batch * p * 2 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    for (int b = 0; b < batch; ++b) {
+        if (p_succ) p_succ[b] = h_scr[2 * b];
+        for (int l = 0; l < p; ++l) {
+            const double *g = h_scr + 2 * batch + 2 * ((size_t)b * p + l);
+            dbeta[(size_t)b * p + l] = -2.0 * sign * g[0];
+            dgamma[(size_t)b * p + l] = 2.0 * g[1];
+        }
+    }
+    return QAOA_OK;
+}
+
+template <typename R>
+static int grad_small(int batch, int n, const uint8_t *cost, int m, int p, const double *gamma, const double *beta,
+                      int flags, double *d_scr, double *h_scr, cudaStream_t stream, double *p_succ, double *dgamma,
+                      double *dbeta) {
+    int rc = adj_init<R>();
+    if (rc) return rc;
+    const int sign = (flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    const size_t tab_n = (size_t)p * (m + 1);
+    double *h_tab = h_scr;
+    double *h_coef = h_tab + 2 * tab_n;
+    for (int l = 0; l < p; ++l) {
+        for (int k = 0; k <= m; ++k) {
+            h_tab[2 * ((size_t)l * (m + 1) + k)] = std::cos(gamma[l] * k);
+            h_tab[2 * ((size_t)l * (m + 1) + k) + 1] = -std::sin(gamma[l] * k);
+        }
+        h_coef[2 * l] = std::cos(beta[l]);
+        h_coef[2 * l + 1] = sign * std::sin(beta[l]);
+    }
+    const size_t in_bytes = (2 * tab_n + 2 * (size_t)p) * sizeof(double);
+    double *d_tab = d_scr, *d_coef = d_scr + 2 * tab_n;
+    double *d_out = d_scr + 2 * tab_n + 2 * p;
+    const size_t out_n = (size_t)batch * 2 * (1 + p);
+    QAOA_CUDA_TRY(cudaMemcpyAsync(d_scr, h_scr, in_bytes, cudaMemcpyHostToDevice, stream));
+    const size_t smem = 2 * sizeof(typename Cx<R>::V) * (size_t(1) << n) + (size_t(1) << n);
+    profile_before(K_SMALL_N, stream);
+    small_grad_kernel<R><<<batch, PT, smem, stream>>>(cost, n, m, p, d_tab, d_coef, d_out);
+    if ((rc = profile_after(K_SMALL_N, stream))) return rc;
+    double *h_out = h_scr + 2 * tab_n + 2 * p;
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, out_n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    for (int b = 0; b < batch; ++b) {
+        const double *o = h_out + (size_t)b * 2 * (1 + p);
+        if (p_succ) p_succ[b] = o[0];
+        for (int l = 0; l < p; ++l) {
+            dbeta[(size_t)b * p + l] = -2.0 * sign * o[2 * (1 + l)];
+            dgamma[(size_t)b * p + l] = 2.0 * o[2 * (1 + l) + 1];
+        }
+    }
+    return QAOA_OK;
+}
+
+static int grad_common(int batch, int n, const uint8_t *cost, int m, int p, const double *gamma, const double *beta,
+                       int dtype, int flags, void *state, void *adj, double *p_succ, double *dgamma, double *dbeta,
+                       void *stream_) {
+    if (batch < 1) return set_error(QAOA_EINVAL, "batch=%d", batch);
+    if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", dtype);
+    const int nmax = dtype == QAOA_C64 ? QAOA_MAX_N : QAOA_MAX_N - 1;
+    if (n < 1 || n > nmax) return set_error(QAOA_ERANGE, "n=%d outside [1, %d]", n, nmax);
+    if (m < 0 || m > QAOA_MAX_M) return set_error(QAOA_ERANGE, "m=%d", m);
+    if (p < 1) return set_error(QAOA_EINVAL, "gradient needs p >= 1 (p=%d)", p);
+    if (!cost || !state || !adj || !gamma || !beta || !dgamma || !dbeta) return set_error(QAOA_EINVAL, "NULL argument");
+    for (int l = 0; l < p; ++l)
+        if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l])) return set_error(QAOA_EINVAL, "angle %d not finite", l);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    Scratch *sc = nullptr;
+    int rc;
+    if (n <= small_n_limit(dtype)) {
+        const size_t words = 2 * (size_t)p * (m + 1) + 2 * (size_t)p + (size_t)batch * 2 * (1 + p) + 16;
+        if ((rc = scratch_for(stream, words * sizeof(double), words * sizeof(double), &sc))) return rc;
+        if (dtype == QAOA_C64)
+            return grad_small<float>(batch, n, cost, m, p, gamma, beta, flags, (double *)sc->dev, (double *)sc->host,
+                                     stream, p_succ, dgamma, dbeta);
+        return grad_small<double>(batch, n, cost, m, p, gamma, beta, flags, (double *)sc->dev, (double *)sc->host,
+                                  stream, p_succ, dgamma, dbeta);
+    }
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    const int gxf = pass_grid_x(dtype, n, batch);
+    const size_t gxa = (size_t)di.sms * 2 + 1;
+    const size_t words = (size_t)batch * gxf * 2 + (size_t)batch * 2 + (size_t)batch * p * gxa * 2 +
+                         (size_t)batch * p * 2 + 64;
+    const size_t hwords = (size_t)batch * 2 + (size_t)batch * p * 2 + 16;
+    if ((rc = scratch_for(stream, words * sizeof(double), hwords * sizeof(double), &sc))) return rc;
+    if (dtype == QAOA_C64)
+        return grad_passes<float>(batch, n, cost, m, p, gamma, beta, dtype, flags, state, adj, (double *)sc->dev,
+                                  (double *)sc->host, stream, p_succ, dgamma, dbeta);
+    return grad_passes<double>(batch, n, cost, m, p, gamma, beta, dtype, flags, state, adj, (double *)sc->dev,
+                               (double *)sc->host, stream, p_succ, dgamma, dbeta);
+}
+
+}  // namespace qaoa
+
+using namespace qaoa;
+
+extern "C" int qaoa_grad(int n, const uint8_t *d_cost, int m, int p, const double *gamma, const double *beta, int dtype,
+                         int flags, void *d_state, void *d_adj, double *p_succ, double *dgamma, double *dbeta,
+                         void *stream) {
+    return grad_common(1, n, d_cost, m, p, gamma, beta, dtype, flags, d_state, d_adj, p_succ, dgamma, dbeta, stream);
+}
+
+extern "C" int qaoa_grad_batch(int batch, int n, const uint8_t *d_costs, int m_max, int p, const double *gamma,
+                               const double *beta, int dtype, int flags, void *d_states, void *d_adjs, double *p_succ,
+                               double *dgamma, double *dbeta, void *stream) {
+    return grad_common(batch, n, d_costs, m_max, p, gamma, beta, dtype, flags, d_states, d_adjs, p_succ, dgamma, dbeta,
+                       stream);
+}

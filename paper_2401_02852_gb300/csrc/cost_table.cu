@@ -1,0 +1,373 @@
+// K1: the NAE cost table C(x) (Eq. for C^NAE, Sec. "Problem Hamiltonian"; its
+// De Morgan form in Appendix A.2: a clause is violated when its literals are
+// all false or all true).
+//
+// Bit-sliced design.  A thread owns one 32-bit word of assignments,
+// x = 32 X + b for b = 0..31.  Variables 0..4 vary inside the word, variables
+// >= 5 are constant across it.  Per clause the host precomputes
+//   hi_mask / hi_neg : the clause's variables >= 5 and their negations,
+//   all_true  : bit b set iff every literal on a variable < 5 is true at b,
+//   all_false : bit b set iff every such literal is false at b.
+// With t = ((32 X) ^ hi_neg) & hi_mask (the literal values on the high
+// variables) the clause's violation word is
+//   V = (t == 0 ? all_false : 0) | (t == hi_mask ? all_true : 0),
+// i.e. all literals false, or all true.  The 32 per-x counts are kept as
+// bit planes by a carry-save (Harley-Seal) adder over chunks of 16 clauses,
+// then transposed to bytes with 8x8 bit-matrix transposes.  The number of
+// solutions (count 0) and the largest count come out of the same pass.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "qaoa_internal.cuh"
+
+namespace qaoa {
+
+constexpr int CT_THREADS = 256;
+
+struct CostParams {
+    int n, m;
+    ClauseRec rec[QAOA_MAX_M];
+};
+
+__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+__device__ __forceinline__ uint32_t violation_word(uint32_t xh, const ClauseRec &r) {
+    const uint32_t t = (xh ^ r.hi_neg) & r.hi_mask;
+    return (t == 0u ? r.all_false : 0u) | (t == r.hi_mask ? r.all_true : 0u);
+}
+
+// Counts violated clauses for the 32 assignments of word X; planes[q] holds bit q
+// of every count (q = 0..9, counts up to 1023).
+template <class Rec>
+__device__ __forceinline__ void count_word(uint32_t X, int m, const Rec &rec, uint32_t planes[10]) {
+    const uint32_t xh = X << 5;
+    uint32_t ones = 0, twos = 0, fours = 0, eights = 0;
+    uint32_t up[6] = {0, 0, 0, 0, 0, 0};
+    for (int i0 = 0; i0 < m; i0 += 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = (i0 + j < m) ? violation_word(xh, rec(i0 + j)) : 0u;
+        uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+        csa(twosA, ones, ones, v[0], v[1]);
+        csa(twosB, ones, ones, v[2], v[3]);
+        csa(foursA, twos, twos, twosA, twosB);
+        csa(twosA, ones, ones, v[4], v[5]);
+        csa(twosB, ones, ones, v[6], v[7]);
+        csa(foursB, twos, twos, twosA, twosB);
+        csa(eightsA, fours, fours, foursA, foursB);
+        csa(twosA, ones, ones, v[8], v[9]);
+        csa(twosB, ones, ones, v[10], v[11]);
+        csa(foursA, twos, twos, twosA, twosB);
+        csa(twosA, ones, ones, v[12], v[13]);
+        csa(twosB, ones, ones, v[14], v[15]);
+        csa(foursB, twos, twos, twosA, twosB);
+        csa(eightsB, fours, fours, foursA, foursB);
+        csa(sixteens, eights, eights, eightsA, eightsB);
+        uint32_t carry = sixteens;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const uint32_t t = up[q] & carry;
+            up[q] ^= carry;
+            carry = t;
+        }
+    }
+    planes[0] = ones;
+    planes[1] = twos;
+    planes[2] = fours;
+    planes[3] = eights;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) planes[4 + q] = up[q];
+}
+
+// 8x8 bit transpose of a 64-bit word (byte j = row j, bit i = column i).
+__device__ __forceinline__ uint64_t transpose8(uint64_t w) {
+    uint64_t t;
+    t = (w ^ (w >> 7)) & 0x00AA00AA00AA00AAull;
+    w ^= t ^ (t << 7);
+    t = (w ^ (w >> 14)) & 0x0000CCCC0000CCCCull;
+    w ^= t ^ (t << 14);
+    t = (w ^ (w >> 28)) & 0x00000000F0F0F0F0ull;
+    w ^= t ^ (t << 28);
+    return w;
+}
+
+// Byte b of the result (b = 0..31) = bits 0..7 of the count of x = 32 X + b.
+__device__ __forceinline__ void planes_to_bytes(const uint32_t planes[10], uint32_t out[8]) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        // row j of the 8x8 block = byte g of plane j
+        const uint32_t lo = __byte_perm(__byte_perm(planes[0], planes[1], 0x0040 + g * 0x0011),
+                                        __byte_perm(planes[2], planes[3], 0x0040 + g * 0x0011), 0x5410);
+        const uint32_t hi = __byte_perm(__byte_perm(planes[4], planes[5], 0x0040 + g * 0x0011),
+                                        __byte_perm(planes[6], planes[7], 0x0040 + g * 0x0011), 0x5410);
+        const uint64_t w = transpose8(((uint64_t)hi << 32) | lo);
+        out[2 * g] = (uint32_t)w;
+        out[2 * g + 1] = (uint32_t)(w >> 32);
+    }
+}
+
+template <class Rec>
+__device__ __forceinline__ void cost_table_body(int n, int m, const Rec &rec, uint8_t *cost,
+                                                unsigned long long *stats) {
+    const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
+    const uint32_t valid = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
+    unsigned long long nsol = 0;
+    uint32_t mx = 0;
+    for (uint64_t X = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; X < words;
+         X += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t planes[10];
+        count_word((uint32_t)X, m, rec, planes);
+        uint32_t bytes[8];
+        planes_to_bytes(planes, bytes);
+        uint32_t any = 0;
+#pragma unroll
+        for (int q = 0; q < 10; ++q) any |= planes[q];
+        nsol += __popc(~any & valid);
+        // largest count among the valid lanes
+        const uint32_t over = (planes[8] | planes[9]) & valid;
+        uint32_t bm = 0;
+        if (n >= 5) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) bm = __vmaxu4(bm, bytes[q]);
+            bm = max(max(bm & 0xFF, (bm >> 8) & 0xFF), max((bm >> 16) & 0xFF, bm >> 24));
+        } else {
+            for (uint32_t b = 0; b < (1u << n); ++b) bm = max(bm, (bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+        }
+        if (over) {  // some count >= 256: take those lanes exactly
+            for (uint32_t b = 0; b < 32; ++b)
+                if ((over >> b) & 1u) {
+                    uint32_t c = 0;
+                    for (int q = 0; q < 10; ++q) c |= ((planes[q] >> b) & 1u) << q;
+                    bm = max(bm, c);
+                }
+        }
+        mx = max(mx, bm);
+        if (n >= 5) {
+            uint4 *dst = reinterpret_cast<uint4 *>(cost + 32 * X);
+            dst[0] = make_uint4(bytes[0], bytes[1], bytes[2], bytes[3]);
+            dst[1] = make_uint4(bytes[4], bytes[5], bytes[6], bytes[7]);
+        } else {
+            for (uint32_t b = 0; b < (1u << n); ++b) cost[b] = (uint8_t)((bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+        }
+    }
+    // warp then block reduction, one atomic pair per block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nsol += __shfl_xor_sync(0xFFFFFFFFu, nsol, o);
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    }
+    __shared__ unsigned long long s_sol[CT_THREADS / 32];
+    __shared__ uint32_t s_max[CT_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_sol[wid] = nsol;
+        s_max[wid] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0;
+        uint32_t b = 0;
+        for (int w = 0; w < CT_THREADS / 32; ++w) {
+            a += s_sol[w];
+            b = max(b, s_max[w]);
+        }
+        if (a) atomicAdd(&stats[0], a);
+        atomicMax(&stats[1], (unsigned long long)b);
+    }
+}
+
+struct ParamRec {
+    const CostParams *p;
+    __device__ __forceinline__ ClauseRec operator()(int i) const { return p->rec[i]; }
+};
+struct GlobalRec {
+    const ClauseRec *r;
+    __device__ __forceinline__ ClauseRec operator()(int i) const {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(r + i));
+        return ClauseRec{v.x, v.y, v.z, v.w};
+    }
+};
+
+__global__ void __launch_bounds__(CT_THREADS) cost_table_kernel(const __grid_constant__ CostParams prm, uint8_t *cost,
+                                                                unsigned long long *stats) {
+    ParamRec rec{&prm};
+    cost_table_body(prm.n, prm.m, rec, cost, stats);
+}
+
+// Batched tables.  With ns == nullptr every instance has n qubits and its table
+// at costs + inst 2^n; otherwise instance inst has ns[inst] qubits and its table
+// at costs + offs[inst].
+__global__ void __launch_bounds__(CT_THREADS) cost_table_batch_kernel(int n, const int *ns, const uint64_t *offs,
+                                                                      const ClauseRec *recs, const int *ms,
+                                                                      int m_stride, uint8_t *costs,
+                                                                      unsigned long long *stats) {
+    const int inst = blockIdx.y;
+    GlobalRec rec{recs + (size_t)inst * m_stride};
+    const int ni = ns ? ns[inst] : n;
+    uint8_t *dst = ns ? costs + offs[inst] : costs + ((size_t)inst << n);
+    cost_table_body(ni, ms[inst], rec, dst, stats + 2 * inst);
+}
+
+// ---------------------------------------------------------------------------
+int validate_instance(const naesat_instance *inst) {
+    if (!inst) return set_error(QAOA_EINVAL, "instance is NULL");
+    const int n = inst->n, m = inst->m, k = inst->k;
+    if (n < 1 || n > QAOA_MAX_N) return set_error(QAOA_ERANGE, "n=%d outside [1, %d]", n, QAOA_MAX_N);
+    if (m < 0 || m > QAOA_MAX_M) return set_error(QAOA_ERANGE, "m=%d outside [0, %d]", m, QAOA_MAX_M);
+    if (m == 0) return QAOA_OK;
+    if (k < 1 || k > n) return set_error(QAOA_ERANGE, "k=%d outside [1, n=%d]", k, n);
+    if (!inst->var || !inst->neg) return set_error(QAOA_EINVAL, "var/neg is NULL");
+    for (int i = 0; i < m; ++i) {
+        uint64_t seen = 0;
+        for (int j = 0; j < k; ++j) {
+            const int v = inst->var[(size_t)i * k + j];
+            const int s = inst->neg[(size_t)i * k + j];
+            if (v < 0 || v >= n) return set_error(QAOA_EINVAL, "clause %d: variable %d outside [0, %d)", i, v, n);
+            if (s != 0 && s != 1) return set_error(QAOA_EINVAL, "clause %d: negation flag %d not 0/1", i, s);
+            if ((seen >> v) & 1ull) return set_error(QAOA_EINVAL, "clause %d: variable %d repeated", i, v);
+            seen |= 1ull << v;
+        }
+    }
+    return QAOA_OK;
+}
+
+int encode_instance(const naesat_instance *inst, ClauseRec *out) {
+    const int m = inst->m, k = inst->k;
+    for (int i = 0; i < m; ++i) {
+        uint32_t mask = 0, negp = 0;
+        for (int j = 0; j < k; ++j) {
+            const int v = inst->var[(size_t)i * k + j];
+            mask |= 1u << v;
+            negp |= (uint32_t)inst->neg[(size_t)i * k + j] << v;
+        }
+        uint32_t at = 0, af = 0;
+        for (uint32_t b = 0; b < 32; ++b) {
+            bool all_t = true, all_f = true;
+            for (int j = 0; j < k; ++j) {
+                const int v = inst->var[(size_t)i * k + j];
+                if (v >= 5) continue;
+                const uint32_t lit = ((b >> v) & 1u) ^ (uint32_t)inst->neg[(size_t)i * k + j];
+                all_t = all_t && lit == 1u;
+                all_f = all_f && lit == 0u;
+            }
+            at |= (uint32_t)all_t << b;
+            af |= (uint32_t)all_f << b;
+        }
+        out[i] = ClauseRec{mask & ~31u, negp & ~31u, at, af};
+    }
+    return QAOA_OK;
+}
+
+static int grid_for(uint64_t words, int batch) {
+    DeviceInfo di;
+    if (device_info(&di)) return -1;
+    const uint64_t need = (words + CT_THREADS - 1) / CT_THREADS;
+    uint64_t cap = (uint64_t)di.sms * 8 * 4;
+    cap = cap / (uint64_t)batch + 1;
+    return (int)(need < cap ? need : cap);
+}
+
+int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d_offs, const ClauseRec *d_recs,
+                            const int *d_m, int m_stride, uint8_t *d_costs, unsigned long long *d_stats,
+                            cudaStream_t stream) {
+    const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
+    const int gx = grid_for(words, batch);
+    if (gx < 0) return QAOA_ECUDA;
+    profile_before(K_COST_TABLE, stream);
+    cost_table_batch_kernel<<<dim3(gx, batch), CT_THREADS, 0, stream>>>(n, d_ns, d_offs, d_recs, d_m, m_stride, d_costs,
+                                                                        d_stats);
+    return profile_after(K_COST_TABLE, stream);
+}
+
+int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned long long *d_stats,
+                          cudaStream_t stream) {
+    std::vector<char> buf(sizeof(CostParams));
+    CostParams *prm = reinterpret_cast<CostParams *>(buf.data());
+    prm->n = inst->n;
+    prm->m = inst->m;
+    encode_instance(inst, prm->rec);
+    const uint64_t words = inst->n >= 5 ? (1ull << (inst->n - 5)) : 1ull;
+    const int gx = grid_for(words, 1);
+    if (gx < 0) return QAOA_ECUDA;
+    profile_before(K_COST_TABLE, stream);
+    cost_table_kernel<<<gx, CT_THREADS, 0, stream>>>(*prm, d_cost, d_stats);
+    return profile_after(K_COST_TABLE, stream);
+}
+
+}  // namespace qaoa
+
+using namespace qaoa;
+
+extern "C" int naesat_cost_table(const naesat_instance *inst, uint8_t *d_cost, uint64_t *n_sol, uint32_t *max_cost,
+                                 void *stream_) {
+    int rc = validate_instance(inst);
+    if (rc) return rc;
+    if (!d_cost) return set_error(QAOA_EINVAL, "d_cost is NULL");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    Scratch *sc = nullptr;
+    rc = scratch_for(stream, 64, 64, &sc);
+    if (rc) return rc;
+    unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(sc->dev);
+    QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 2 * sizeof(unsigned long long), stream));
+    rc = launch_cost_table_one(inst, d_cost, d_stats, stream);
+    if (rc) return rc;
+    if (!n_sol && !max_cost && inst->m <= 255) return QAOA_OK;
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(sc->host);
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h, d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (n_sol) *n_sol = h[0];
+    if (max_cost) *max_cost = (uint32_t)h[1];
+    if (h[1] > 255) return set_error(QAOA_ERANGE, "max C = %llu does not fit the uint8 table", h[1]);
+    return QAOA_OK;
+}
+
+extern "C" int naesat_cost_table_batch(int batch, const naesat_instance *insts, uint8_t *d_costs, uint64_t *n_sol,
+                                       uint32_t *max_cost, void *stream_) {
+    if (batch < 1 || !insts || !d_costs) return set_error(QAOA_EINVAL, "batch/insts/d_costs");
+    const int n = insts[0].n;
+    int m_stride = 1;
+    for (int b = 0; b < batch; ++b) {
+        int rc = validate_instance(&insts[b]);
+        if (rc) return rc;
+        if (insts[b].n != n) return set_error(QAOA_EINVAL, "batch instances differ in n");
+        m_stride = insts[b].m > m_stride ? insts[b].m : m_stride;
+    }
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const size_t rec_bytes = (size_t)batch * m_stride * sizeof(ClauseRec);
+    const size_t m_bytes = ((size_t)batch * sizeof(int) + 255) & ~(size_t)255;
+    const size_t stat_bytes = (size_t)batch * 2 * sizeof(unsigned long long);
+    Scratch *sc = nullptr;
+    int rc = scratch_for(stream, rec_bytes + m_bytes + stat_bytes + 512, rec_bytes + m_bytes + stat_bytes + 512, &sc);
+    if (rc) return rc;
+    char *hbase = reinterpret_cast<char *>(sc->host);
+    char *dbase = reinterpret_cast<char *>(sc->dev);
+    ClauseRec *h_recs = reinterpret_cast<ClauseRec *>(hbase);
+    int *h_m = reinterpret_cast<int *>(hbase + rec_bytes);
+    for (int b = 0; b < batch; ++b) {
+        encode_instance(&insts[b], h_recs + (size_t)b * m_stride);
+        h_m[b] = insts[b].m;
+    }
+    QAOA_CUDA_TRY(cudaMemcpyAsync(dbase, hbase, rec_bytes + m_bytes, cudaMemcpyHostToDevice, stream));
+    unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(dbase + rec_bytes + m_bytes);
+    QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, stat_bytes, stream));
+    rc = launch_cost_table_batch(batch, n, nullptr, nullptr, reinterpret_cast<const ClauseRec *>(dbase),
+                                 reinterpret_cast<const int *>(dbase + rec_bytes), m_stride, d_costs, d_stats, stream);
+    if (rc) return rc;
+    unsigned long long *h_stats = reinterpret_cast<unsigned long long *>(hbase + rec_bytes + m_bytes);
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h_stats, d_stats, stat_bytes, cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));  // the pinned staging block is reused by the next call
+    int status = QAOA_OK;
+    for (int b = 0; b < batch; ++b) {
+        if (n_sol) n_sol[b] = h_stats[2 * b];
+        if (max_cost) max_cost[b] = (uint32_t)h_stats[2 * b + 1];
+        if (h_stats[2 * b + 1] > 255 && status == QAOA_OK)
+            status = set_error(QAOA_ERANGE, "instance %d: max C = %llu does not fit the uint8 table", b, h_stats[2 * b + 1]);
+    }
+    return status;
+}

@@ -1,0 +1,650 @@
+// K2/K3/K4/K6: the QAOA layers U_B(beta) U_C(gamma) on a state in HBM.
+//
+//  * U_C(gamma) = diag(exp(-i gamma C(x))) (Eq. for U_C; Appendix A.3's
+//    diagonalisation): C(x) takes at most m + 1 values, so the phase is a lookup
+//    in a per-layer table T[c] (FP64 on the host, cast to the state's type),
+//    fused into the load of the layer's first pass.
+//  * U_B(beta) = prod_j [cos(beta) I + i sin(beta) X_j] (Appendix A.3): one
+//    butterfly per qubit over the pairs (x, x xor 2^j).  The qubit factors
+//    commute, so a layer is split into HBM passes over groups of qubits: the
+//    low pass (tile bits = state bits [0, T)) and high passes over strided rows.
+//  * p_succ = sum_{C(x)=0} |psi(x)|^2 and the norm (Def. of the success
+//    probability): accumulated in the store of the last pass, per-block FP64
+//    partials, then a fixed-order reduction (deterministic).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "pass_common.cuh"
+#include "qaoa_internal.cuh"
+
+namespace qaoa {
+
+template <typename R>
+struct PassArgs {
+    typename Cx<R>::V *state;  // instance 0; instance b at state + b 2^n
+    typename Cx<R>::V *adj;    // nullable: receives P psi in the store
+    const uint8_t *cost;
+    double *partials;          // [batch][gridDim.x][2] when reduce
+    int n, row, lo, m;
+    uint32_t active;           // tile bits to butterfly
+    int init, reduce, unit_a;
+    R A, B;
+    uint64_t tiles;            // tiles per instance
+};
+
+template <typename R, int NT>
+struct PhaseTab {
+    typename Cx<R>::V t[NT];
+};
+
+template <typename R, bool LOW, bool PHASE, bool UA>
+__device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
+                                           typename Cx<R>::V *tile) {
+    using V = typename Cx<R>::V;
+    constexpr int T = Cx<R>::T, RB = Cx<R>::RB, NR = 1 << RB;
+    constexpr int LC = LOW ? Cx<R>::LC_LOW : Cx<R>::LC_HIGH;
+    const uint32_t tid = threadIdx.x;
+    const size_t inst = blockIdx.y;
+    V *st = a.state + (inst << a.n);
+    V *adj = a.adj ? a.adj + (inst << a.n) : nullptr;
+    const uint8_t *cs = a.cost + (inst << a.n);
+    // Every tile address is thread pointer + r * stride (the plan keeps the row
+    // width at 4 bits in high passes, so the register bits are all strided).
+    const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<Cx<R>, 8>(tid, 0), a.row, a.lo);
+    const uint64_t ld_s = LOW ? 256u : (1ull << (a.lo + 8 - a.row));
+    const uint64_t st_t = elem_offset(tile_elem<Cx<R>, LC>(tid, 0), a.row, a.lo);
+    const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
+    double acc[2] = {0.0, 0.0};  // p_succ, norm
+    for (uint64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+        const uint64_t base = tile_base(t, a.row, a.lo, T);
+        V v[NR];
+        // load (mapping 8: coalesced), phase fused
+        {
+            const V *lp = st + base + ld_t;
+            const uint8_t *lc = cs + base + ld_t;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (PHASE && a.init) {
+                    v[r] = stab[lc[r * ld_s]];
+                } else {
+                    v[r] = lp[r * ld_s];
+                    if (PHASE) v[r] = cmul(v[r], stab[lc[r * ld_s]]);
+                }
+            }
+        }
+        reg_butterflies<Cx<R>, UA, 8, T>(v, a.active, a.A, a.B);
+        if (LOW) {
+            exchange<Cx<R>, 8, 0>(v, tile);
+            reg_butterflies<Cx<R>, UA, 0, T>(v, a.active, a.A, a.B);
+            exchange<Cx<R>, 0, LC>(v, tile);
+        } else {
+            exchange<Cx<R>, 8, LC>(v, tile);
+        }
+        reg_butterflies<Cx<R>, UA, LC, 8>(v, a.active, a.A, a.B);
+        // store (mapping LC: coalesced), reduction fused
+        R ps = 0, nm = 0;
+        {
+            V *sp = st + base + st_t;
+            asm volatile("" : "+l"(sp));  // keep the store addresses out of the load phase
+            const uint8_t *sc = cs + base + st_t;
+            V *sa = adj ? adj + base + st_t : nullptr;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                sp[r * st_s] = v[r];
+                if (a.reduce) {
+                    const R w = v[r].x * v[r].x + v[r].y * v[r].y;
+                    nm += w;
+                    const bool sol = sc[r * st_s] == 0;
+                    if (sol) ps += w;
+                    if (sa) {
+                        V z;
+                        z.x = sol ? v[r].x : R(0);
+                        z.y = sol ? v[r].y : R(0);
+                        sa[r * st_s] = z;
+                    }
+                }
+            }
+        }
+        acc[0] += (double)ps;
+        acc[1] += (double)nm;
+    }
+    if (a.reduce) {
+        block_sum<2>(acc);
+        if (threadIdx.x == 0) {
+            double *out = a.partials + 2 * (inst * gridDim.x + blockIdx.x);
+            out[0] = acc[0];
+            out[1] = acc[1];
+        }
+    }
+}
+
+template <typename R, bool LOW, bool PHASE, int NT>
+__global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
+                                                     const __grid_constant__ PhaseTab<R, NT> tab) {
+    using V = typename Cx<R>::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    V *stab = tile + (1 << Cx<R>::T);
+    if (PHASE) {  // 256 entries at least: any uint8 cost indexes inside the table
+        for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
+            V z;
+            z.x = z.y = 0;
+            stab[i] = i <= a.m ? tab.t[i] : z;
+        }
+        __syncthreads();
+    }
+    if (a.unit_a)
+        pass_tiles<R, LOW, PHASE, true>(a, stab, tile);
+    else
+        pass_tiles<R, LOW, PHASE, false>(a, stab, tile);
+}
+
+// Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
+__global__ void __launch_bounds__(PT) reduce_partials_kernel(const double *part, int nblk, int nv, double *out) {
+    const size_t b = blockIdx.x;
+    double x[4] = {0, 0, 0, 0};
+    for (int j = threadIdx.x; j < nblk; j += PT)
+        for (int k = 0; k < nv; ++k) x[k] += part[(b * nblk + j) * nv + k];
+    block_sum<4>(x);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nv; ++k) out[b * nv + k] = x[k];
+}
+
+int launch_reduce(const double *part, int groups, int nblk, int nv, double *out, cudaStream_t stream) {
+    profile_before(K_REDUCE, stream);
+    reduce_partials_kernel<<<groups, PT, 0, stream>>>(part, nblk, nv, out);
+    return profile_after(K_REDUCE, stream);
+}
+
+// Standalone p_succ / norm of a state (Def. of the success probability).
+template <typename R>
+__global__ void __launch_bounds__(PT) psucc_kernel(const typename Cx<R>::V *st, const uint8_t *cs, int n,
+                                                   double *partials) {
+    constexpr int CH = 32;  // elements per thread per chunk (FP32 inner sum for c64)
+    const uint64_t N = 1ull << n;
+    const uint64_t chunk = (uint64_t)PT * CH;
+    double acc[2] = {0.0, 0.0};
+    for (uint64_t c0 = (uint64_t)blockIdx.x * chunk; c0 < N; c0 += (uint64_t)gridDim.x * chunk) {
+        R ps = 0, nm = 0;
+#pragma unroll 8
+        for (int r = 0; r < CH; ++r) {
+            const uint64_t g = c0 + (uint64_t)r * PT + threadIdx.x;
+            if (g < N) {
+                const typename Cx<R>::V v = st[g];
+                const R w = v.x * v.x + v.y * v.y;
+                nm += w;
+                if (cs[g] == 0) ps += w;
+            }
+        }
+        acc[0] += (double)ps;
+        acc[1] += (double)nm;
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = acc[0];
+        partials[2 * blockIdx.x + 1] = acc[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K6: whole evolution of one small instance per CTA, state resident in shared
+// memory.  Tables are FP64 complex [p][m+1] and coefficients [p][4]
+// (A, B, unit_a, unused) in device memory.
+template <typename R>
+__device__ __forceinline__ void smem_butterfly_pass(typename Cx<R>::V *s, int n, int j, int two, R A, R B,
+                                                    bool ua) {
+    using V = typename Cx<R>::V;
+    const uint32_t groups = 1u << (n - 1 - two);
+    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        if (two) {
+            const uint32_t x0 = ((g >> j) << (j + 2)) | (g & ((1u << j) - 1u));
+            const uint32_t h1 = 1u << j, h2 = 2u << j;
+            V a = s[x0], b = s[x0 | h1], c = s[x0 | h2], d = s[x0 | h1 | h2];
+            if (ua) {
+                bfly<true>(a, b, A, B);
+                bfly<true>(c, d, A, B);
+                bfly<true>(a, c, A, B);
+                bfly<true>(b, d, A, B);
+            } else {
+                bfly<false>(a, b, A, B);
+                bfly<false>(c, d, A, B);
+                bfly<false>(a, c, A, B);
+                bfly<false>(b, d, A, B);
+            }
+            s[x0] = a;
+            s[x0 | h1] = b;
+            s[x0 | h2] = c;
+            s[x0 | h1 | h2] = d;
+        } else {
+            const uint32_t x0 = ((g >> j) << (j + 1)) | (g & ((1u << j) - 1u));
+            V a = s[x0], b = s[x0 | (1u << j)];
+            if (ua)
+                bfly<true>(a, b, A, B);
+            else
+                bfly<false>(a, b, A, B);
+            s[x0] = a;
+            s[x0 | (1u << j)] = b;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(PT) small_kernel(const SmallJob *jobs, const double *tables, const double *coefs,
+                                                   int max_n) {
+    using V = typename Cx<R>::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmallJob jb = jobs[blockIdx.x];
+    const int n = jb.n;
+    const uint32_t N = 1u << n;
+    V *s = reinterpret_cast<V *>(smem_raw);
+    V *stab = s + (1u << max_n);
+    uint8_t *sc = reinterpret_cast<uint8_t *>(stab + MAX_TABLE);
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sc[x] = jb.cost[x];
+    for (int l = 0; l < jb.p; ++l) {
+        const double *tb = tables + 2 * ((size_t)jb.table_off + (size_t)l * (jb.m + 1));
+        __syncthreads();
+        for (int c = threadIdx.x; c <= jb.m; c += blockDim.x) {
+            V z;
+            z.x = (R)tb[2 * c];
+            z.y = (R)tb[2 * c + 1];
+            stab[c] = z;
+        }
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) s[x] = l == 0 ? stab[sc[x]] : cmul(s[x], stab[sc[x]]);
+        const double *cf = coefs + 4 * ((size_t)jb.coef_off + l);
+        const R A = (R)cf[0], B = (R)cf[1];
+        const bool ua = cf[2] != 0.0;
+        for (int j = 0; j < n; j += 2) {
+            __syncthreads();
+            smem_butterfly_pass<R>(s, n, j, (j + 1 < n) ? 1 : 0, A, B, ua);
+        }
+    }
+    if (jb.p == 0) {  // |+>: the table of "layer 0" holds the amplitude
+        const double *tb = tables + 2 * (size_t)jb.table_off;
+        V z;
+        z.x = (R)tb[0];
+        z.y = (R)tb[1];
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) s[x] = z;
+    }
+    __syncthreads();
+    double acc[2] = {0.0, 0.0};
+    V *out = reinterpret_cast<V *>(jb.state);
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+        const V v = s[x];
+        const double w = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        acc[1] += w;
+        if (sc[x] == 0) acc[0] += w;
+        if (out) out[x] = v;
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0 && jb.result) {
+        jb.result[0] = acc[0];
+        jb.result[1] = acc[1];
+    }
+}
+
+int small_n_limit(int dtype) { return dtype == QAOA_C64 ? Cx<float>::T : Cx<double>::T; }
+int small_n_pack_limit(int dtype) { return dtype == QAOA_C64 ? 14 : 13; }
+
+static size_t small_smem(int dtype, int max_n) {
+    const size_t es = dtype == QAOA_C64 ? sizeof(float2) : sizeof(double2);
+    return es * ((size_t(1) << max_n) + MAX_TABLE) + (size_t(1) << max_n);
+}
+
+int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const double *d_tables, const double *d_coefs,
+                       int max_n, int flags, cudaStream_t stream) {
+    (void)flags;
+    const size_t smem = small_smem(dtype, max_n);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        const int big = (int)small_smem(QAOA_C128, small_n_pack_limit(QAOA_C128));
+        cudaError_t e1 = cudaFuncSetAttribute(small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)small_smem(QAOA_C64, small_n_pack_limit(QAOA_C64)));
+        cudaError_t e2 = cudaFuncSetAttribute(small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        attr_err = e1 != cudaSuccess ? e1 : e2;
+    });
+    if (attr_err != cudaSuccess) return cuda_error(attr_err, "small_kernel attributes");
+    profile_before(K_SMALL_N, stream);
+    if (dtype == QAOA_C64)
+        small_kernel<float><<<n_jobs, PT, smem, stream>>>(d_jobs, d_tables, d_coefs, max_n);
+    else
+        small_kernel<double><<<n_jobs, PT, smem, stream>>>(d_jobs, d_tables, d_coefs, max_n);
+    return profile_after(K_SMALL_N, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the multi-pass evolution.
+
+template <typename R>
+static size_t pass_smem(bool phase, int m) {
+    return sizeof(typename Cx<R>::V) * ((size_t(1) << Cx<R>::T) + (phase ? (size_t)(m < 255 ? 256 : m + 1) : 0));
+}
+
+template <typename R>
+struct PassKernels {
+    using Full = PhaseTab<R, MAX_TABLE>;
+    using None = PhaseTab<R, 1>;
+    int blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [low][phase]
+    cudaError_t init() {
+        const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(pass_kernel<R, true, true, MAX_TABLE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+            return e;
+        if ((e = cudaFuncSetAttribute(pass_kernel<R, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+            return e;
+        if ((e = cudaFuncSetAttribute(pass_kernel<R, false, true, MAX_TABLE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+            return e;
+        if ((e = cudaFuncSetAttribute(pass_kernel<R, false, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      big)))
+            return e;
+        const size_t s_phase = pass_smem<R>(true, 255), s_plain = pass_smem<R>(false, 0);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[1][1],
+                                                               pass_kernel<R, true, true, MAX_TABLE>, PT, s_phase)))
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[1][0], pass_kernel<R, true, false, 1>, PT,
+                                                               s_plain)))
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[0][1],
+                                                               pass_kernel<R, false, true, MAX_TABLE>, PT, s_phase)))
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[0][0], pass_kernel<R, false, false, 1>,
+                                                               PT, s_plain)))
+            return e;
+        return cudaSuccess;
+    }
+};
+
+template <typename R>
+static int pass_kernels(PassKernels<R> **out) {
+    static std::mutex mu;
+    static PassKernels<R> pk;
+    static int state = 0;  // 0 = not yet, 1 = ok, <0 = failed
+    std::lock_guard<std::mutex> lk(mu);
+    if (state == 0) {
+        cudaError_t e = pk.init();
+        state = e == cudaSuccess ? 1 : -1;
+        if (e != cudaSuccess) return cuda_error(e, "pass kernel attributes");
+    }
+    if (state < 0) return set_error(QAOA_ECUDA, "pass kernels unavailable");
+    *out = &pk;
+    return QAOA_OK;
+}
+
+// Grid width per instance: enough CTAs to fill every SM, capped by the tiles.
+static int grid_x(int sms, int per_sm, int batch, uint64_t tiles) {
+    uint64_t want = (uint64_t)sms * (per_sm > 0 ? per_sm : 1);
+    want = (want + batch - 1) / batch;
+    if (want < 1) want = 1;
+    return (int)(want < tiles ? want : tiles);
+}
+
+int pass_grid_x(int dtype, int n, int batch) {
+    DeviceInfo di;
+    if (device_info(&di)) return -1;
+    const int T = dtype == QAOA_C64 ? Cx<float>::T : Cx<double>::T;
+    return grid_x(di.sms, 2, batch, 1ull << (n - T));
+}
+
+template <typename R>
+static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStream_t stream) {
+    using V = typename Cx<R>::V;
+    PassKernels<R> *pk = nullptr;
+    int rc = pass_kernels<R>(&pk);
+    if (rc) return rc;
+    Plan pl;
+    rc = make_plan(r.n, r.dtype, &pl);
+    if (rc) return rc;
+    constexpr int T = Cx<R>::T;
+    const int sign = (r.flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    const bool want = r.d_result != nullptr;
+    const int p_eff = r.p > 0 ? r.p : 1;
+    std::vector<double> re(r.m + 1), im(r.m + 1);
+    // The phase table is large: keep it off the stack.
+    std::vector<char> tbuf(sizeof(typename PassKernels<R>::Full));
+    auto *tab = reinterpret_cast<typename PassKernels<R>::Full *>(tbuf.data());
+    typename PassKernels<R>::None none{};
+    const dim3 block(PT);
+    for (int l = 0; l < p_eff; ++l) {
+        LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+        double scale = std::pow(k.sigma, r.n);
+        if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
+        phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());
+        for (int c = 0; c <= r.m; ++c) {
+            tab->t[c].x = (R)re[c];
+            tab->t[c].y = (R)im[c];
+        }
+        const int np = r.p > 0 ? pl.n_passes : 1;
+        for (int i = 0; i < np; ++i) {
+            const Pass &ps = pl.pass[i];
+            PassArgs<R> a;
+            a.state = reinterpret_cast<V *>(r.state);
+            a.cost = r.cost;
+            a.partials = d_partials;
+            a.n = r.n;
+            a.m = r.m;
+            if (i == 0) {  // low pass: the whole tile is one contiguous row
+                a.row = T;
+                a.lo = T;
+                a.active = r.p > 0 ? ((1u << T) - 1u) : 0u;
+            } else {
+                a.row = ps.row;
+                a.lo = ps.lo;
+                a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
+            }
+            a.init = (l == 0 && i == 0) ? 1 : 0;
+            const bool last = (l == p_eff - 1 && i == np - 1);
+            a.reduce = (last && (want || r.adj)) ? 1 : 0;
+            a.adj = (last && r.adj) ? reinterpret_cast<V *>(r.adj) : nullptr;
+            a.unit_a = k.unit_a ? 1 : 0;
+            a.A = (R)k.A;
+            a.B = (R)k.B;
+            a.tiles = 1ull << (r.n - T);
+            const dim3 grid(gx, r.batch);
+            if (i == 0) {
+                profile_before(K_PASS_LOW, stream);
+                pass_kernel<R, true, true, MAX_TABLE>
+                    <<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+                rc = profile_after(K_PASS_LOW, stream);
+            } else {
+                profile_before(K_PASS_HIGH, stream);
+                pass_kernel<R, false, false, 1><<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+                rc = profile_after(K_PASS_HIGH, stream);
+            }
+            if (rc) return rc;
+        }
+    }
+    if (want) {
+        profile_before(K_REDUCE, stream);
+        reduce_partials_kernel<<<r.batch, PT, 0, stream>>>(d_partials, gx, 2, r.d_result);
+        rc = profile_after(K_REDUCE, stream);
+    }
+    return rc;
+}
+
+// Small-n path of evolve_device: tables and coefficients through scratch.
+static int evolve_small(const EvolveReq &r, Scratch *sc, size_t off, cudaStream_t stream) {
+    const int sign = (r.flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    const int pl = r.p > 0 ? r.p : 1;
+    const size_t tab_n = (size_t)pl * (r.m + 1);
+    char *hb = reinterpret_cast<char *>(sc->host) + off;
+    char *db = reinterpret_cast<char *>(sc->dev) + off;
+    double *h_tab = reinterpret_cast<double *>(hb);
+    double *h_coef = h_tab + 2 * tab_n;
+    SmallJob *h_jobs = reinterpret_cast<SmallJob *>(h_coef + 4 * pl);
+    std::vector<double> re(r.m + 1), im(r.m + 1);
+    for (int l = 0; l < pl; ++l) {
+        LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+        double scale = std::pow(k.sigma, r.n);
+        if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
+        phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());
+        for (int c = 0; c <= r.m; ++c) {
+            h_tab[2 * ((size_t)l * (r.m + 1) + c)] = re[c];
+            h_tab[2 * ((size_t)l * (r.m + 1) + c) + 1] = im[c];
+        }
+        h_coef[4 * l] = k.A;
+        h_coef[4 * l + 1] = k.B;
+        h_coef[4 * l + 2] = k.unit_a ? 1.0 : 0.0;
+        h_coef[4 * l + 3] = 0.0;
+    }
+    const size_t es = r.dtype == QAOA_C64 ? 8 : 16;
+    for (int b = 0; b < r.batch; ++b) {
+        SmallJob j;
+        j.cost = r.cost + ((size_t)b << r.n);
+        j.state = reinterpret_cast<char *>(r.state) + ((size_t)b << r.n) * es;
+        j.result = r.d_result ? r.d_result + 2 * b : nullptr;
+        j.n = r.n;
+        j.m = r.m;
+        j.p = r.p;
+        j.table_off = 0;
+        j.coef_off = 0;
+        h_jobs[b] = j;
+    }
+    const size_t bytes = (2 * tab_n + 4 * (size_t)pl) * sizeof(double) + (size_t)r.batch * sizeof(SmallJob);
+    QAOA_CUDA_TRY(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, stream));
+    int rc = launch_small_batch(r.dtype, r.batch, reinterpret_cast<SmallJob *>(db + (2 * tab_n + 4 * pl) * sizeof(double)),
+                                reinterpret_cast<double *>(db), reinterpret_cast<double *>(db) + 2 * tab_n, r.n, r.flags,
+                                stream);
+    if (rc) return rc;
+    // the pinned staging block is reused by the next call on this stream
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    return QAOA_OK;
+}
+
+// Validates an evolution request (shared by the ABI entry points).
+static int validate_evolve(int batch, int n, const uint8_t *cost, int m, int p, const double *gamma,
+                           const double *beta, int dtype, void *state) {
+    if (batch < 1) return set_error(QAOA_EINVAL, "batch=%d", batch);
+    if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", dtype);
+    const int nmax = dtype == QAOA_C64 ? QAOA_MAX_N : QAOA_MAX_N - 1;
+    if (n < 1 || n > nmax) return set_error(QAOA_ERANGE, "n=%d outside [1, %d]", n, nmax);
+    if (m < 0 || m > QAOA_MAX_M) return set_error(QAOA_ERANGE, "m=%d outside [0, %d]", m, QAOA_MAX_M);
+    if (p < 0) return set_error(QAOA_EINVAL, "p=%d", p);
+    if (p > 0 && (!gamma || !beta)) return set_error(QAOA_EINVAL, "gamma/beta NULL");
+    for (int l = 0; l < p; ++l)
+        if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l]))
+            return set_error(QAOA_EINVAL, "angle %d is not finite", l);
+    if (!cost || !state) return set_error(QAOA_EINVAL, "d_cost/d_state NULL");
+    return QAOA_OK;
+}
+
+int evolve_device_impl(const EvolveReq &r, cudaStream_t stream, double *d_partials, int gx) {
+    if (r.dtype == QAOA_C64) return evolve_passes<float>(r, d_partials, gx, stream);
+    return evolve_passes<double>(r, d_partials, gx, stream);
+}
+
+}  // namespace qaoa
+
+using namespace qaoa;
+
+// Runs an evolution and (optionally) copies the FP64 results to the host.
+static int evolve_common(int batch, int n, const uint8_t *d_cost, int m, int p, const double *gamma,
+                         const double *beta, int dtype, int flags, void *d_state, double *p_succ, double *norm,
+                         void *adj, void *stream_) {
+    int rc = validate_evolve(batch, n, d_cost, m, p, gamma, beta, dtype, d_state);
+    if (rc) return rc;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const bool want = p_succ || norm;
+    EvolveReq r{batch, n, m, p, dtype, flags, d_cost, d_state, adj, gamma, beta, nullptr};
+    Scratch *sc = nullptr;
+    if (n <= small_n_limit(dtype) && !adj) {
+        const int pl = p > 0 ? p : 1;
+        const size_t stage = (2 * (size_t)pl * (m + 1) + 4 * (size_t)pl) * sizeof(double) +
+                             (size_t)batch * sizeof(SmallJob) + 256;
+        const size_t res = (size_t)batch * 2 * sizeof(double);
+        rc = scratch_for(stream, stage + res, stage + res, &sc);
+        if (rc) return rc;
+        if (want) r.d_result = reinterpret_cast<double *>(reinterpret_cast<char *>(sc->dev) + stage);
+        rc = evolve_small(r, sc, 0, stream);
+        if (rc || !want) return rc;
+        double *h = reinterpret_cast<double *>(reinterpret_cast<char *>(sc->host) + stage);
+        QAOA_CUDA_TRY(cudaMemcpyAsync(h, r.d_result, res, cudaMemcpyDeviceToHost, stream));
+        QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+        for (int b = 0; b < batch; ++b) {
+            if (p_succ) p_succ[b] = h[2 * b];
+            if (norm) norm[b] = h[2 * b + 1];
+        }
+        return QAOA_OK;
+    }
+    if (n <= small_n_limit(dtype)) return set_error(QAOA_ERANGE, "n=%d too small for the pass path", n);
+    const int gx = pass_grid_x(dtype, n, batch);
+    if (gx < 0) return QAOA_ECUDA;
+    const size_t part = (size_t)batch * gx * 2 * sizeof(double);
+    const size_t res = (size_t)batch * 2 * sizeof(double);
+    rc = scratch_for(stream, part + res + 256, res + 64, &sc);
+    if (rc) return rc;
+    double *d_part = reinterpret_cast<double *>(sc->dev);
+    if (want) r.d_result = reinterpret_cast<double *>(reinterpret_cast<char *>(sc->dev) + part);
+    rc = evolve_device_impl(r, stream, d_part, gx);
+    if (rc || !want) return rc;
+    double *h = reinterpret_cast<double *>(sc->host);
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h, r.d_result, res, cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    for (int b = 0; b < batch; ++b) {
+        if (p_succ) p_succ[b] = h[2 * b];
+        if (norm) norm[b] = h[2 * b + 1];
+    }
+    return QAOA_OK;
+}
+
+namespace qaoa {
+int evolve_with_adjoint_seed(int batch, int n, const uint8_t *d_cost, int m, int p, const double *gamma,
+                             const double *beta, int dtype, int flags, void *d_state, void *d_adj, double *p_succ,
+                             void *stream) {
+    return evolve_common(batch, n, d_cost, m, p, gamma, beta, dtype, flags, d_state, p_succ, nullptr, d_adj, stream);
+}
+}  // namespace qaoa
+
+extern "C" int qaoa_evolve(int n, const uint8_t *d_cost, int m, int p, const double *gamma, const double *beta,
+                           int dtype, int flags, void *d_state, double *p_succ, double *norm, void *stream) {
+    return evolve_common(1, n, d_cost, m, p, gamma, beta, dtype, flags, d_state, p_succ, norm, nullptr, stream);
+}
+
+extern "C" int qaoa_evolve_batch(int batch, int n, const uint8_t *d_costs, int m_max, int p, const double *gamma,
+                                 const double *beta, int dtype, int flags, void *d_states, double *p_succ,
+                                 double *norm, void *stream) {
+    return evolve_common(batch, n, d_costs, m_max, p, gamma, beta, dtype, flags, d_states, p_succ, norm, nullptr,
+                         stream);
+}
+
+extern "C" int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_state, int dtype, double *p_succ,
+                                 double *norm, void *stream_) {
+    if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", dtype);
+    if (n < 1 || n > QAOA_MAX_N) return set_error(QAOA_ERANGE, "n=%d", n);
+    if (!d_cost || !d_state || !p_succ || !norm) return set_error(QAOA_EINVAL, "NULL argument");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    DeviceInfo di;
+    int rc = device_info(&di);
+    if (rc) return rc;
+    const uint64_t chunks = ((1ull << n) + (uint64_t)PT * 32 - 1) / ((uint64_t)PT * 32);
+    uint64_t g = (uint64_t)di.sms * 8;
+    const int grid = (int)(chunks < g ? chunks : g);
+    const size_t part = (size_t)grid * 2 * sizeof(double);
+    Scratch *sc = nullptr;
+    rc = scratch_for(stream, part + 64, 64, &sc);
+    if (rc) return rc;
+    double *d_part = reinterpret_cast<double *>(sc->dev);
+    double *d_res = reinterpret_cast<double *>(reinterpret_cast<char *>(sc->dev) + part);
+    profile_before(K_PSUCC, stream);
+    if (dtype == QAOA_C64)
+        psucc_kernel<float><<<grid, PT, 0, stream>>>(reinterpret_cast<const float2 *>(d_state), d_cost, n, d_part);
+    else
+        psucc_kernel<double><<<grid, PT, 0, stream>>>(reinterpret_cast<const double2 *>(d_state), d_cost, n, d_part);
+    rc = profile_after(K_PSUCC, stream);
+    if (rc) return rc;
+    profile_before(K_REDUCE, stream);
+    reduce_partials_kernel<<<1, PT, 0, stream>>>(d_part, grid, 2, d_res);
+    rc = profile_after(K_REDUCE, stream);
+    if (rc) return rc;
+    double *h = reinterpret_cast<double *>(sc->host);
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h, d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    *p_succ = h[0];
+    *norm = h[1];
+    return QAOA_OK;
+}

@@ -1,0 +1,164 @@
+// Device building blocks of the HBM butterfly passes (forward and adjoint).
+//
+// A pass streams the state through shared memory one tile at a time.  A tile
+// holds 2^T amplitudes: 2^row contiguous ones (a row) times 2^(T - row) rows
+// strided by 2^lo, so its tile bits [row, T) are the state bits
+// [lo, lo + T - row) that the pass butterflies ("the group"); the low pass has
+// row = lo = T and butterflies state bits [0, T).
+//
+// 256 threads own the tile in registers, 2^RB amplitudes each.  A "mapping"
+// (parameter LO) gives thread tid and register r the tile element
+//   u = (tid & (2^LO - 1)) | ((tid >> LO) << (LO + RB)) | (r << LO),
+// so the registers of a thread span tile bits [LO, LO + RB) and the butterflies
+// on those bits run in registers.  Moving between mappings goes through shared
+// memory with an XOR swizzle that keeps every round free of bank conflicts.
+//   mapping 8       : lanes run along tile bits 0..4 -> coalesced loads/stores
+//   mapping 0       : the low pass's tile bits [0, RB)
+//   mapping LC      : the rest, also coalesced (lanes along bits 0..3 or 0..4)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace qaoa {
+
+constexpr int PT = 256;  // threads per pass CTA (8 thread bits)
+
+// Tile geometry: element type R, 2^T amplitudes per tile, 2^RB per thread.
+// LC_LOW / LC_HIGH are the store mappings of the low and high passes; the
+// swizzle spreads the bits that lanes run along over the shared-memory banks
+// (checked conflict-free for every mapping used).
+template <typename R, int T_, int RB_>
+struct Geo {
+    using V = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    using Real = R;
+    static constexpr int T = T_;
+    static constexpr int RB = RB_;
+    static constexpr int NR = 1 << RB_;
+    static constexpr int LC_LOW = RB_;  // after the rounds at 8 and 0
+    static constexpr int LC_HIGH = 4;
+    static constexpr int SW_SHIFT = RB_;
+    static constexpr uint32_t SW_MASK = sizeof(R) == 4 ? 15u : 7u;
+    static_assert(T_ - RB_ == 8, "256 threads own the tile");
+    __device__ static __forceinline__ uint32_t swz(uint32_t u) { return u ^ ((u >> SW_SHIFT) & SW_MASK); }
+};
+
+// Forward geometry: 64 KiB tiles (2^13 complex64 / 2^12 complex128).
+template <typename R>
+struct FwdGeoT;
+template <>
+struct FwdGeoT<float> {
+    using type = Geo<float, 13, 5>;
+};
+template <>
+struct FwdGeoT<double> {
+    using type = Geo<double, 12, 4>;
+};
+template <typename R>
+using Cx = typename FwdGeoT<R>::type;
+
+template <typename G, int LO>
+__device__ __forceinline__ uint32_t tile_elem(uint32_t tid, uint32_t r) {
+    constexpr int RB = G::RB;
+    return (tid & ((1u << LO) - 1u)) | ((tid >> LO) << (LO + RB)) | (r << LO);
+}
+
+// State index of tile element u (relative to the tile base).
+__device__ __forceinline__ uint64_t elem_offset(uint32_t u, int row, int lo) {
+    return (uint64_t)(u & ((1u << row) - 1u)) | ((uint64_t)(u >> row) << lo);
+}
+
+// State index of the first element of tile t: the tile id fills the free bits
+// [row, lo) and [lo + G, n), G = T - row.
+__device__ __forceinline__ uint64_t tile_base(uint64_t t, int row, int lo, int T) {
+    const int G = T - row;
+    const int span = lo - row;
+    return ((t & ((1ull << span) - 1ull)) << row) | ((t >> span) << (lo + G));
+}
+
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Mixer butterfly in factored form: (a, b) <- (A a + i B b, i B a + A b) with
+// A = 1 (UA) or B = 1; the dropped scalar sigma^n is folded into the phase table.
+template <bool UA, typename V, typename R>
+__device__ __forceinline__ void bfly(V &a, V &b, R A, R B) {
+    V na, nb;
+    if (UA) {
+        na.x = fma(-B, b.y, a.x);
+        na.y = fma(B, b.x, a.y);
+        nb.x = fma(-B, a.y, b.x);
+        nb.y = fma(B, a.x, b.y);
+    } else {
+        na.x = fma(A, a.x, -b.y);
+        na.y = fma(A, a.y, b.x);
+        nb.x = fma(A, b.x, -a.y);
+        nb.y = fma(A, b.y, a.x);
+    }
+    a = na;
+    b = nb;
+}
+
+// Butterflies on the register bits of mapping LO whose tile bits are in `mask`
+// (bits LO + q, q = 0..RB-1) and below `below` (compile-time exclusion of bits
+// done in an earlier round).
+template <typename G, bool UA, int LO, int BELOW>
+__device__ __forceinline__ void reg_butterflies(typename G::V *v, uint32_t mask, typename G::Real A,
+                                                typename G::Real B) {
+    constexpr int RB = G::RB;
+    constexpr int NR = 1 << RB;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+        if (LO + q < BELOW && ((mask >> (LO + q)) & 1u)) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i)
+                if (!(i & (1 << q))) bfly<UA>(v[i], v[i | (1 << q)], A, B);
+        }
+    }
+}
+
+// Re-distribute the tile from mapping FROM to mapping TO through shared memory.
+template <typename G, int FROM, int TO>
+__device__ __forceinline__ void exchange(typename G::V *v, typename G::V *tile) {
+    constexpr int NR = G::NR;
+    const uint32_t tid = threadIdx.x;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NR; ++r) tile[G::swz(tile_elem<G, FROM>(tid, r))] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = tile[G::swz(tile_elem<G, TO>(tid, r))];
+}
+
+// FP64 block reduction of NV values per thread; thread 0 gets the sums.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&x)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x[k] += __shfl_xor_sync(0xFFFFFFFFu, x[k], o);
+    __shared__ double s_red[PT / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s_red[wid][k] = x[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < PT / 32; ++w) s += s_red[w][k];
+            x[k] = s;
+        }
+    }
+}
+
+}  // namespace qaoa

@@ -1,0 +1,263 @@
+// Host runtime of the library: errors, device facts, scratch, instrumentation,
+// pass planning and the FP64 per-layer coefficients.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "qaoa_internal.cuh"
+
+namespace qaoa {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    return set_error(QAOA_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// ---------------------------------------------------------------------------
+static std::mutex g_dev_mu;
+static std::map<int, DeviceInfo> g_devs;
+
+int device_info(DeviceInfo *out) {
+    int dev = 0;
+    QAOA_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_devs.find(dev);
+    if (it == g_devs.end()) {
+        DeviceInfo d;
+        d.device = dev;
+        QAOA_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        int optin = 0;
+        QAOA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        d.smem_optin = (size_t)optin;
+        it = g_devs.emplace(dev, d).first;
+    }
+    *out = it->second;
+    return QAOA_OK;
+}
+
+// ---------------------------------------------------------------------------
+static std::mutex g_scratch_mu;
+static std::map<std::pair<int, cudaStream_t>, Scratch> g_scratch;
+
+int scratch_for(cudaStream_t stream, size_t dev_bytes, size_t host_bytes, Scratch **out) {
+    int dev = 0;
+    QAOA_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    Scratch &s = g_scratch[{dev, stream}];
+    if (s.dev_bytes < dev_bytes) {
+        // The stream may still use the old block: wait for it before freeing.
+        QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (s.dev) cudaFree(s.dev);
+        s.dev = nullptr;
+        s.dev_bytes = 0;
+        size_t want = dev_bytes < (1u << 20) ? (1u << 20) : dev_bytes + dev_bytes / 4;
+        if (cudaMalloc(&s.dev, want) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QAOA_ENOMEM, "scratch: cudaMalloc(%zu) failed", want);
+        }
+        s.dev_bytes = want;
+    }
+    if (s.host_bytes < host_bytes) {
+        QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (s.host) cudaFreeHost(s.host);
+        s.host = nullptr;
+        s.host_bytes = 0;
+        size_t want = host_bytes < 4096 ? 4096 : host_bytes;
+        if (cudaMallocHost(&s.host, want) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QAOA_ENOMEM, "scratch: cudaMallocHost(%zu) failed", want);
+        }
+        s.host_bytes = want;
+    }
+    *out = &s;
+    return QAOA_OK;
+}
+
+static int release_all_scratch() {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_scratch) {
+        cudaSetDevice(kv.first.first);
+        cudaDeviceSynchronize();
+        if (kv.second.dev) cudaFree(kv.second.dev);
+        if (kv.second.host) cudaFreeHost(kv.second.host);
+    }
+    g_scratch.clear();
+    cudaSetDevice(cur);
+    return QAOA_OK;
+}
+
+// ---------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<bool> g_profile{false};
+static std::mutex g_prof_mu;
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+static thread_local cudaEvent_t t_pending = nullptr;
+
+static const char *k_names[K_NUM_KINDS] = {
+    "cost_table", "pass_low", "pass_high", "small_n", "reduce",
+    "success_prob", "adjoint_low", "adjoint_high", "adjoint_seed", "serve_small"};
+
+static cudaEvent_t take_event() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void profile_before(int kind, cudaStream_t stream) {
+    (void)kind;
+    if (!g_profile.load(std::memory_order_relaxed)) return;
+    t_pending = take_event();
+    cudaEventRecord(t_pending, stream);
+}
+
+int profile_after(int kind, cudaStream_t stream) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, k_names[kind]);
+    if (g_profile.load(std::memory_order_relaxed) && t_pending) {
+        cudaEvent_t b = take_event();
+        cudaEventRecord(b, stream);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof.push_back({kind, t_pending, b});
+        t_pending = nullptr;
+    }
+    return QAOA_OK;
+}
+
+// ---------------------------------------------------------------------------
+int make_plan_geo(int n, int T, int G, Plan *plan) {
+    if (n < T + 1 || n > QAOA_MAX_N) return set_error(QAOA_ERANGE, "plan: n=%d outside [%d, %d]", n, T + 1, QAOA_MAX_N);
+    plan->n = n;
+    plan->tile_bits = T;
+    plan->pass[0] = {0, T, T};
+    // High passes all span G bits with rows of T - G contiguous amplitudes; the
+    // last group ends at bit n, so it may re-cover already mixed bits, which it
+    // carries without butterflies (`bits` counts only the new ones).
+    int np = 0;
+    for (int lo = T; lo < n; lo += G) {
+        if (1 + np >= 8) return set_error(QAOA_ERANGE, "plan: n=%d needs too many passes", n);
+        const int glo = lo + G <= n ? lo : n - G;
+        plan->pass[1 + np] = {glo, lo + G <= n ? G : n - lo, T - G};
+        ++np;
+    }
+    plan->n_passes = 1 + np;
+    return QAOA_OK;
+}
+
+int make_plan(int n, int dtype, Plan *plan) {
+    if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype %d", dtype);
+    return dtype == QAOA_C64 ? make_plan_geo(n, T_C64, G_MAX_C64, plan) : make_plan_geo(n, T_C128, G_MAX_C128, plan);
+}
+
+LayerCoef layer_coef(double beta, int sign) {
+    const double c = std::cos(beta), sn = std::sin(beta);
+    const double S = sign * sn;  // butterfly: a' = c a + i S b, b' = i S a + c b
+    LayerCoef k;
+    if (std::fabs(c) >= std::fabs(S)) {
+        k.sigma = c;
+        k.A = 1.0;
+        k.B = S / c;
+        k.unit_a = true;
+    } else {
+        k.sigma = S;
+        k.A = c / S;
+        k.B = 1.0;
+        k.unit_a = false;
+    }
+    return k;
+}
+
+void phase_table(double gamma, double scale, int m, double *re, double *im) {
+    for (int c = 0; c <= m; ++c) {
+        re[c] = scale * std::cos(gamma * (double)c);
+        im[c] = -scale * std::sin(gamma * (double)c);
+    }
+}
+
+}  // namespace qaoa
+
+using namespace qaoa;
+
+extern "C" {
+
+const char *qaoa_last_error(void) { return g_err; }
+
+int qaoa_version(void) { return 100; }
+
+int qaoa_release_scratch(void) { return release_all_scratch(); }
+
+int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits) {
+    Plan pl;
+    int rc = make_plan(n, dtype, &pl);
+    if (rc) return rc;
+    for (int i = 0; i < pl.n_passes; ++i) {
+        if (group_lo) group_lo[i] = pl.pass[i].lo;
+        if (group_bits) group_bits[i] = pl.pass[i].bits;
+        if (row_bits) row_bits[i] = pl.pass[i].row;
+    }
+    return pl.n_passes;
+}
+
+int qaoa_profile_enable(int on) {
+    g_profile.store(on != 0);
+    return QAOA_OK;
+}
+
+int qaoa_profile_read(int max_kinds, uint64_t *launches, double *ms) {
+    for (int i = 0; i < max_kinds; ++i) {
+        if (launches) launches[i] = 0;
+        if (ms) ms[i] = 0.0;
+    }
+    QAOA_CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        if (r.kind < max_kinds) {
+            if (launches) launches[r.kind] += 1;
+            if (ms) ms[r.kind] += t;
+        }
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    return K_NUM_KINDS;
+}
+
+const char *qaoa_kernel_name(int kind) {
+    if (kind < 0 || kind >= K_NUM_KINDS) return "";
+    return k_names[kind];
+}
+
+uint64_t qaoa_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

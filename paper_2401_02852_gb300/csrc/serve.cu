@@ -1,0 +1,539 @@
+// Serving loop: continuous batching of whole QAOA evaluations (not in the
+// paper; a serving pattern around its simulation).
+//
+// One scheduler thread per server.  Requests are copied at submit time and
+// queued.  Each scheduler iteration (1) retires finished work by querying CUDA
+// events, (2) admits waiting requests in arrival order while a slot (a CUDA
+// stream with its own staging) is free and the device-memory footprint fits
+// the budget:
+//   * requests with n <= small_n_max are packed, up to max_batch at a time, into
+//     one batched cost-table launch plus one small-n evolution launch (one CTA
+//     per request, state resident in shared memory, any n and p per request);
+//   * larger requests run alone on a slot: cost table, then the multi-pass
+//     evolution with the fused p_succ reduction.
+// Device memory for tables and states comes from cudaMallocAsync on the slot's
+// stream and returns with cudaFreeAsync, so admission never synchronises the
+// device.  Results land in pinned host memory and are published when the
+// slot's completion event fires.  Every wait on the host is bounded.
+#include <cuda_runtime.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "qaoa_internal.cuh"
+
+namespace qaoa {
+
+static uint64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+struct Req {
+    uint64_t ticket;
+    int n, m, k, p;
+    std::vector<int32_t> var;
+    std::vector<uint8_t> neg;
+    std::vector<double> gamma, beta;
+    uint64_t t_submit;
+    size_t footprint;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<std::shared_ptr<Req>> reqs;  // requests in flight on this slot
+    size_t bytes = 0;                        // footprint charged
+    uint64_t t_start = 0;
+    // staging
+    char *h_stage = nullptr, *d_stage = nullptr;
+    size_t stage_cap = 0;
+    double *d_part = nullptr;                // partials for the pass path
+    size_t part_cap = 0;
+    void *d_cost = nullptr, *d_state = nullptr;  // large job buffers (freed async)
+    bool packed = false;                     // the slot runs a packed small-n batch
+    size_t res_off = 0;                      // packed: offset of the stats block in staging
+};
+
+}  // namespace qaoa
+
+struct qaoa_server {
+    qaoa_server_opts o;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<qaoa::Req>> waiting;
+    std::map<uint64_t, qaoa_result> results;   // finished, not yet polled
+    std::map<uint64_t, int> state;             // 0 waiting, 1 running
+    std::vector<qaoa::Slot> slots;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    size_t used_bytes = 0;
+    uint64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // submitted, completed, packed, single, peak, cancelled, errors, jobs
+    int init_status = QAOA_OK;
+};
+
+namespace qaoa {
+
+static size_t es_of(int dtype) { return dtype == QAOA_C64 ? 8 : 16; }
+
+static int ensure_stage(Slot &s, size_t bytes) {
+    if (s.stage_cap >= bytes) return QAOA_OK;
+    if (s.h_stage) cudaFreeHost(s.h_stage);
+    if (s.d_stage) cudaFree(s.d_stage);
+    s.h_stage = s.d_stage = nullptr;
+    s.stage_cap = 0;
+    size_t want = std::max(bytes + bytes / 2, (size_t)1 << 20);
+    QAOA_CUDA_TRY(cudaMallocHost((void **)&s.h_stage, want));
+    QAOA_CUDA_TRY(cudaMalloc((void **)&s.d_stage, want));
+    s.stage_cap = want;
+    return QAOA_OK;
+}
+
+// Launch one large request on slot s (stream ordered, no host sync).
+static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
+    const int dtype = sv->o.dtype;
+    const size_t N = (size_t)1 << q.n;
+    int rc;
+    naesat_instance inst{q.n, q.m, q.k, q.var.data(), q.neg.data()};
+    // results layout in staging: [0..2) stats (u64), [2..4) p_succ, norm
+    if ((rc = ensure_stage(s, 64))) return rc;
+    QAOA_CUDA_TRY(cudaMallocAsync(&s.d_cost, N, s.stream));
+    QAOA_CUDA_TRY(cudaMallocAsync(&s.d_state, N * es_of(dtype), s.stream));
+    unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(s.d_stage);
+    double *d_res = reinterpret_cast<double *>(s.d_stage + 16);
+    QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 16, s.stream));
+    if ((rc = launch_cost_table_one(&inst, (uint8_t *)s.d_cost, d_stats, s.stream))) return rc;
+    const int gx = pass_grid_x(dtype, q.n, 1);
+    if (gx < 0) return QAOA_ECUDA;
+    if (s.part_cap < (size_t)gx * 2) {
+        if (s.d_part) cudaFree(s.d_part);
+        QAOA_CUDA_TRY(cudaMalloc((void **)&s.d_part, (size_t)gx * 2 * sizeof(double)));
+        s.part_cap = (size_t)gx * 2;
+    }
+    EvolveReq r{1, q.n, q.m, q.p, dtype, sv->o.flags, (const uint8_t *)s.d_cost, s.d_state, nullptr,
+                q.gamma.data(), q.beta.data(), d_res};
+    if ((rc = evolve_device_impl(r, s.stream, s.d_part, gx))) return rc;
+    QAOA_CUDA_TRY(cudaMemcpyAsync(s.h_stage, s.d_stage, 32, cudaMemcpyDeviceToHost, s.stream));
+    QAOA_CUDA_TRY(cudaFreeAsync(s.d_cost, s.stream));
+    QAOA_CUDA_TRY(cudaFreeAsync(s.d_state, s.stream));
+    s.d_cost = s.d_state = nullptr;
+    QAOA_CUDA_TRY(cudaEventRecord(s.done, s.stream));
+    return QAOA_OK;
+}
+
+// Launch a packed batch of small requests on slot s.
+static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<Req>> &batch) {
+    const int B = (int)batch.size();
+    const int sign = (sv->o.flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    int m_stride = 1, max_n = 1;
+    size_t tab_n = 0, coef_n = 0, cost_bytes = 0;
+    for (auto &q : batch) {
+        m_stride = std::max(m_stride, q->m);
+        max_n = std::max(max_n, q->n);
+        tab_n += (size_t)std::max(q->p, 1) * (q->m + 1);
+        coef_n += (size_t)std::max(q->p, 1);
+        cost_bytes += ((size_t)1 << q->n);
+    }
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_recs = 0;
+    const size_t o_m = align(o_recs + (size_t)B * m_stride * sizeof(ClauseRec));
+    const size_t o_n = align(o_m + (size_t)B * sizeof(int));
+    const size_t o_off = align(o_n + (size_t)B * sizeof(int));
+    const size_t o_tab = align(o_off + (size_t)B * sizeof(uint64_t));
+    const size_t o_coef = align(o_tab + 2 * tab_n * sizeof(double));
+    const size_t o_jobs = align(o_coef + 4 * coef_n * sizeof(double));
+    const size_t o_up = align(o_jobs + (size_t)B * sizeof(SmallJob));  // end of the uploaded part
+    const size_t o_stats = o_up;
+    const size_t o_res = align(o_stats + (size_t)B * 2 * sizeof(unsigned long long));
+    const size_t total = align(o_res + (size_t)B * 2 * sizeof(double));
+    int rc;
+    if ((rc = ensure_stage(s, total))) return rc;
+    QAOA_CUDA_TRY(cudaMallocAsync(&s.d_cost, cost_bytes, s.stream));
+    char *h = s.h_stage, *d = s.d_stage;
+    ClauseRec *h_recs = reinterpret_cast<ClauseRec *>(h + o_recs);
+    int *h_m = reinterpret_cast<int *>(h + o_m);
+    int *h_n = reinterpret_cast<int *>(h + o_n);
+    uint64_t *h_off = reinterpret_cast<uint64_t *>(h + o_off);
+    double *h_tab = reinterpret_cast<double *>(h + o_tab);
+    double *h_coef = reinterpret_cast<double *>(h + o_coef);
+    SmallJob *h_jobs = reinterpret_cast<SmallJob *>(h + o_jobs);
+    size_t toff = 0, coff = 0, boff = 0;
+    std::vector<double> re, im;
+    for (int b = 0; b < B; ++b) {
+        Req &q = *batch[b];
+        naesat_instance inst{q.n, q.m, q.k, q.var.data(), q.neg.data()};
+        encode_instance(&inst, h_recs + (size_t)b * m_stride);
+        h_m[b] = q.m;
+        h_n[b] = q.n;
+        h_off[b] = boff;
+        const int pl = std::max(q.p, 1);
+        re.resize(q.m + 1);
+        im.resize(q.m + 1);
+        for (int l = 0; l < pl; ++l) {
+            LayerCoef k = q.p > 0 ? layer_coef(q.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+            double scale = std::pow(k.sigma, q.n);
+            if (l == 0) scale *= std::pow(2.0, -0.5 * q.n);
+            phase_table(q.p > 0 ? q.gamma[l] : 0.0, scale, q.m, re.data(), im.data());
+            for (int c = 0; c <= q.m; ++c) {
+                h_tab[2 * (toff + (size_t)l * (q.m + 1) + c)] = re[c];
+                h_tab[2 * (toff + (size_t)l * (q.m + 1) + c) + 1] = im[c];
+            }
+            h_coef[4 * (coff + l)] = k.A;
+            h_coef[4 * (coff + l) + 1] = k.B;
+            h_coef[4 * (coff + l) + 2] = k.unit_a ? 1.0 : 0.0;
+            h_coef[4 * (coff + l) + 3] = 0.0;
+        }
+        SmallJob j;
+        j.cost = reinterpret_cast<const uint8_t *>(s.d_cost) + boff;
+        j.state = nullptr;
+        j.result = reinterpret_cast<double *>(d + o_res) + 2 * b;
+        j.n = q.n;
+        j.m = q.m;
+        j.p = q.p;
+        j.table_off = (int)toff;
+        j.coef_off = (int)coff;
+        h_jobs[b] = j;
+        toff += (size_t)pl * (q.m + 1);
+        coff += pl;
+        boff += (size_t)1 << q.n;
+    }
+    QAOA_CUDA_TRY(cudaMemcpyAsync(d, h, o_up, cudaMemcpyHostToDevice, s.stream));
+    QAOA_CUDA_TRY(cudaMemsetAsync(d + o_stats, 0, (size_t)B * 2 * sizeof(unsigned long long), s.stream));
+    if ((rc = launch_cost_table_batch(B, max_n, reinterpret_cast<int *>(d + o_n), reinterpret_cast<uint64_t *>(d + o_off),
+                                      reinterpret_cast<ClauseRec *>(d + o_recs), reinterpret_cast<int *>(d + o_m),
+                                      m_stride, (uint8_t *)s.d_cost, reinterpret_cast<unsigned long long *>(d + o_stats),
+                                      s.stream)))
+        return rc;
+    if ((rc = launch_small_batch(sv->o.dtype, B, reinterpret_cast<SmallJob *>(d + o_jobs),
+                                 reinterpret_cast<double *>(d + o_tab), reinterpret_cast<double *>(d + o_coef), max_n,
+                                 sv->o.flags, s.stream)))
+        return rc;
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h + o_stats, d + o_stats, total - o_stats, cudaMemcpyDeviceToHost, s.stream));
+    QAOA_CUDA_TRY(cudaFreeAsync(s.d_cost, s.stream));
+    s.d_cost = nullptr;
+    QAOA_CUDA_TRY(cudaEventRecord(s.done, s.stream));
+    s.res_off = o_stats;  // stats [B][2] u64, then (after alignment) results [B][2] f64
+    return QAOA_OK;
+}
+
+static size_t footprint(const qaoa_server *sv, int n, bool packed) {
+    const size_t N = (size_t)1 << n;
+    return packed ? N : N * (1 + es_of(sv->o.dtype));
+}
+
+// Publishes the results of a finished slot (scheduler thread, lock held).
+static void retire(qaoa_server *sv, Slot &s) {
+    const bool packed = s.packed;
+    const uint64_t t = now_ns();
+    const int B = (int)s.reqs.size();
+    for (int b = 0; b < B; ++b) {
+        Req &q = *s.reqs[b];
+        qaoa_result r{};
+        r.t_submit_ns = q.t_submit;
+        r.t_start_ns = s.t_start;
+        r.t_done_ns = t;
+        if (packed) {
+            // layout mirrors launch_packed: stats then results after the uploaded part
+            const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s.h_stage + s.res_off);
+            const double *res = reinterpret_cast<const double *>(
+                s.h_stage + ((s.res_off + (size_t)B * 16 + 255) & ~(size_t)255));
+            r.n_sol = st[2 * b];
+            r.max_cost = (uint32_t)st[2 * b + 1];
+            r.p_succ = res[2 * b];
+            r.norm = res[2 * b + 1];
+        } else {
+            const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s.h_stage);
+            const double *res = reinterpret_cast<const double *>(s.h_stage + 16);
+            r.n_sol = st[0];
+            r.max_cost = (uint32_t)st[1];
+            r.p_succ = res[0];
+            r.norm = res[1];
+        }
+        r.status = r.max_cost > 255 ? QAOA_ERANGE : QAOA_OK;
+        if (r.status) sv->counters[6]++;
+        sv->results[q.ticket] = r;
+        sv->state.erase(q.ticket);
+        sv->counters[1]++;
+    }
+    sv->used_bytes -= s.bytes;
+    s.bytes = 0;
+    s.reqs.clear();
+    s.busy = false;
+}
+
+static void fail_slot(qaoa_server *sv, Slot &s, int code) {
+    const uint64_t t = now_ns();
+    for (auto &q : s.reqs) {
+        qaoa_result r{};
+        r.status = code;
+        r.t_submit_ns = q->t_submit;
+        r.t_start_ns = s.t_start;
+        r.t_done_ns = t;
+        sv->results[q->ticket] = r;
+        sv->state.erase(q->ticket);
+        sv->counters[6]++;
+        sv->counters[1]++;
+    }
+    sv->used_bytes -= s.bytes;
+    s.bytes = 0;
+    s.reqs.clear();
+    s.busy = false;
+}
+
+static void scheduler(qaoa_server *sv) {
+    cudaSetDevice(sv->o.device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        // (1) retire finished slots
+        bool any_busy = false;
+        for (size_t i = 0; i < sv->slots.size(); ++i) {
+            Slot &s = sv->slots[i];
+            if (!s.busy) continue;
+            cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaSuccess) {
+                retire(sv, s);
+                sv->cv_done.notify_all();
+            } else if (e != cudaErrorNotReady) {
+                cudaGetLastError();
+                fail_slot(sv, s, QAOA_ECUDA);
+                sv->cv_done.notify_all();
+            } else {
+                any_busy = true;
+            }
+        }
+        if (sv->stop && sv->waiting.empty() && !any_busy) break;
+        // (2) admit waiting requests in arrival order
+        for (size_t i = 0; i < sv->slots.size() && !sv->waiting.empty(); ++i) {
+            Slot &s = sv->slots[i];
+            if (s.busy) continue;
+            auto head = sv->waiting.front();
+            const bool small = head->n <= sv->o.small_n_max;
+            if (small) {
+                std::vector<std::shared_ptr<Req>> batch;
+                size_t bytes = 0;
+                for (auto it = sv->waiting.begin(); it != sv->waiting.end() && (int)batch.size() < sv->o.max_batch;) {
+                    if ((*it)->n <= sv->o.small_n_max && sv->used_bytes + bytes + (*it)->footprint <= sv->o.hbm_budget_bytes) {
+                        bytes += (*it)->footprint;
+                        batch.push_back(*it);
+                        it = sv->waiting.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                if (batch.empty()) break;  // over budget: wait for retirements
+                s.busy = true;
+                s.bytes = bytes;
+                s.reqs = batch;
+                s.t_start = now_ns();
+                sv->used_bytes += bytes;
+                for (auto &q : batch) sv->state[q->ticket] = 1;
+                sv->counters[2]++;
+                s.packed = true;
+                lk.unlock();
+                int rc = launch_packed(sv, s, batch);
+                lk.lock();
+                if (rc) {
+                    fail_slot(sv, s, rc);
+                    sv->cv_done.notify_all();
+                }
+            } else {
+                if (sv->used_bytes + head->footprint > sv->o.hbm_budget_bytes && sv->used_bytes > 0) break;
+                sv->waiting.pop_front();
+                s.busy = true;
+                s.bytes = head->footprint;
+                s.reqs = {head};
+                s.t_start = now_ns();
+                sv->used_bytes += head->footprint;
+                sv->state[head->ticket] = 1;
+                sv->counters[3]++;
+                s.packed = false;
+                lk.unlock();
+                int rc = launch_large(sv, s, *head);
+                lk.lock();
+                if (rc) {
+                    fail_slot(sv, s, rc);
+                    sv->cv_done.notify_all();
+                }
+            }
+            sv->counters[4] = std::max<uint64_t>(sv->counters[4], sv->used_bytes);
+        }
+        // (3) wait: briefly when work is in flight, otherwise until a submit
+        bool busy = false;
+        for (auto &s : sv->slots) busy = busy || s.busy;
+        if (busy)
+            sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        else if (!sv->stop)
+            sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+}
+
+}  // namespace qaoa
+
+using namespace qaoa;
+
+extern "C" int qaoa_server_create(const qaoa_server_opts *opts, qaoa_server **out) {
+    if (!opts || !out) return set_error(QAOA_EINVAL, "NULL argument");
+    if (opts->dtype != QAOA_C64 && opts->dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", opts->dtype);
+    std::unique_ptr<qaoa_server> sv(new qaoa_server());
+    sv->o = *opts;
+    if (sv->o.max_batch <= 0) sv->o.max_batch = 256;
+    if (sv->o.n_streams <= 0) sv->o.n_streams = 4;
+    if (sv->o.max_n <= 0) sv->o.max_n = 30;
+    const int pack = small_n_pack_limit(sv->o.dtype);
+    if (sv->o.small_n_max <= 0) sv->o.small_n_max = pack;
+    if (sv->o.small_n_max > pack) return set_error(QAOA_ERANGE, "small_n_max=%d above %d", sv->o.small_n_max, pack);
+    // requests between small_n_max and the pass path's lower bound run packed alone
+    if (sv->o.small_n_max < small_n_limit(sv->o.dtype)) sv->o.small_n_max = small_n_limit(sv->o.dtype);
+    QAOA_CUDA_TRY(cudaSetDevice(sv->o.device));
+    if (sv->o.hbm_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        QAOA_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        sv->o.hbm_budget_bytes = fr / 2;
+    }
+    // keep freed stream-ordered allocations in the pool between requests
+    cudaMemPool_t pool;
+    QAOA_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, sv->o.device));
+    uint64_t threshold = UINT64_MAX;
+    QAOA_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
+    sv->slots.resize(sv->o.n_streams);
+    for (auto &s : sv->slots) {
+        QAOA_CUDA_TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+        QAOA_CUDA_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    }
+    qaoa_server *raw = sv.release();
+    raw->worker = std::thread(scheduler, raw);
+    *out = raw;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_serve_submit(qaoa_server *sv, const naesat_instance *inst, int p, const double *gamma,
+                                 const double *beta, uint64_t *ticket) {
+    if (!sv || !ticket) return set_error(QAOA_EINVAL, "NULL argument");
+    int rc = validate_instance(inst);
+    if (rc) return rc;
+    if (inst->n > sv->o.max_n) return set_error(QAOA_ERANGE, "n=%d above the server's max_n=%d", inst->n, sv->o.max_n);
+    if (p < 0 || (p > 0 && (!gamma || !beta))) return set_error(QAOA_EINVAL, "p/gamma/beta");
+    for (int l = 0; l < p; ++l)
+        if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l])) return set_error(QAOA_EINVAL, "angle %d not finite", l);
+    auto q = std::make_shared<Req>();
+    q->n = inst->n;
+    q->m = inst->m;
+    q->k = inst->m > 0 ? inst->k : 1;
+    q->p = p;
+    q->var.assign(inst->var, inst->var + (size_t)inst->m * inst->k);
+    q->neg.assign(inst->neg, inst->neg + (size_t)inst->m * inst->k);
+    q->gamma.assign(gamma, gamma + p);
+    q->beta.assign(beta, beta + p);
+    q->t_submit = now_ns();
+    q->footprint = footprint(sv, q->n, q->n <= sv->o.small_n_max);
+    if (q->footprint > sv->o.hbm_budget_bytes)
+        return set_error(QAOA_ENOMEM, "request footprint %zu exceeds the budget %zu", q->footprint,
+                         sv->o.hbm_budget_bytes);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stop) return set_error(QAOA_ECANCELLED, "server is shutting down");
+        q->ticket = sv->next_ticket++;
+        sv->waiting.push_back(q);
+        sv->state[q->ticket] = 0;
+        sv->counters[0]++;
+        *ticket = q->ticket;
+    }
+    sv->cv_work.notify_one();
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_serve_poll(qaoa_server *sv, uint64_t ticket, qaoa_result *out) {
+    if (!sv || !out) return set_error(QAOA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->results.find(ticket);
+    if (it != sv->results.end()) {
+        *out = it->second;
+        sv->results.erase(it);
+        return QAOA_OK;
+    }
+    if (sv->state.count(ticket)) return QAOA_PENDING;
+    return set_error(QAOA_ENOTFOUND, "ticket %llu unknown or already retired", (unsigned long long)ticket);
+}
+
+extern "C" int qaoa_serve_wait(qaoa_server *sv, uint64_t ticket, qaoa_result *out, double timeout_s) {
+    if (!sv || !out) return set_error(QAOA_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        auto it = sv->results.find(ticket);
+        if (it != sv->results.end()) {
+            *out = it->second;
+            sv->results.erase(it);
+            return QAOA_OK;
+        }
+        if (!sv->state.count(ticket))
+            return set_error(QAOA_ENOTFOUND, "ticket %llu unknown or already retired", (unsigned long long)ticket);
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && std::chrono::steady_clock::now() >= deadline) {
+            if (sv->results.count(ticket)) continue;
+            return set_error(QAOA_ETIMEOUT, "ticket %llu not done after %.3f s", (unsigned long long)ticket, timeout_s);
+        }
+    }
+}
+
+extern "C" int qaoa_serve_cancel(qaoa_server *sv, uint64_t ticket) {
+    if (!sv) return set_error(QAOA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto it = sv->waiting.begin(); it != sv->waiting.end(); ++it) {
+        if ((*it)->ticket == ticket) {
+            qaoa_result r{};
+            r.status = QAOA_ECANCELLED;
+            r.t_submit_ns = (*it)->t_submit;
+            r.t_done_ns = now_ns();
+            sv->results[ticket] = r;
+            sv->state.erase(ticket);
+            sv->waiting.erase(it);
+            sv->counters[5]++;
+            sv->cv_done.notify_all();
+            return QAOA_OK;
+        }
+    }
+    if (sv->state.count(ticket)) return QAOA_PENDING;
+    return set_error(QAOA_ENOTFOUND, "ticket %llu unknown", (unsigned long long)ticket);
+}
+
+extern "C" int qaoa_server_stats(qaoa_server *sv, uint64_t *counters) {
+    if (!sv || !counters) return set_error(QAOA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (int i = 0; i < 8; ++i) counters[i] = sv->counters[i];
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_server_destroy(qaoa_server *sv) {
+    if (!sv) return set_error(QAOA_EINVAL, "NULL argument");
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->o.device);
+    for (auto &s : sv->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.h_stage) cudaFreeHost(s.h_stage);
+        if (s.d_stage) cudaFree(s.d_stage);
+        if (s.d_part) cudaFree(s.d_part);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    delete sv;
+    return QAOA_OK;
+}

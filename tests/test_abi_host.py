@@ -1,0 +1,98 @@
+"""Host-only checks of the C ABI: the library builds, loads and exports every
+function that include/qaoa.h declares; host logic (planning, validation) runs
+without a GPU.  No call here launches device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2401_02852_gb300 import _build, _lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "qaoa.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\([^;{]*\)\s*;", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("naesat_cost_table", "qaoa_evolve", "qaoa_success_prob", "qaoa_grad", "qaoa_serve_submit",
+                     "qaoa_serve_poll"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the Python binding binds exactly the declared set
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_version_and_kernel_names(lib):
+    assert lib.qaoa_version() >= 100
+    names = [lib.qaoa_kernel_name(i).decode() for i in range(16)]
+    assert "pass_low" in names and "cost_table" in names
+
+
+def _plan(lib, n, dtype):
+    lo = (ctypes.c_int * 8)()
+    bits = (ctypes.c_int * 8)()
+    row = (ctypes.c_int * 8)()
+    k = lib.qaoa_plan(n, dtype, lo, bits, row)
+    return k, [(lo[i], bits[i], row[i]) for i in range(max(k, 0))]
+
+
+@pytest.mark.parametrize("dtype,T,G", [(0, 13, 9), (1, 12, 8)])
+def test_plan_covers_every_qubit_once(lib, dtype, T, G):
+    for n in range(T + 1, 33):
+        k, passes = _plan(lib, n, dtype)
+        assert k == len(passes) >= 2
+        mixed = list(range(passes[0][1]))
+        assert passes[0] == (0, T, T)
+        for lo, bits, row in passes[1:]:
+            assert row == T - G and lo >= row and lo + G <= n
+            mixed += list(range(lo + G - bits, lo + G))  # the top `bits` of the group
+        assert sorted(mixed) == list(range(n)), (n, passes)
+
+
+def test_plan_rejects_out_of_range(lib):
+    assert lib.qaoa_plan(50, 0, None, None, None) == _lib_code("ERANGE")
+    assert lib.qaoa_plan(20, 7, None, None, None) == _lib_code("EINVAL")
+    assert b"dtype" in lib.qaoa_last_error()
+
+
+def _lib_code(name):
+    return {v: k for k, v in _lib.ERRORS.items()}[name]
+
+
+def test_argument_validation_precedes_device_work(lib):
+    """Invalid calls return their error from host validation, before any CUDA call."""
+    assert lib.naesat_cost_table(None, None, None, None, None) == _lib_code("EINVAL")
+    var = np.array([[0, 0, 1]], dtype=np.int32)  # repeated variable
+    neg = np.zeros((1, 3), dtype=np.uint8)
+    inst = _lib.NaesatInstance(4, 1, 3, var.ctypes.data, neg.ctypes.data)
+    assert lib.naesat_cost_table(ctypes.byref(inst), ctypes.c_void_p(1), None, None, None) == _lib_code("EINVAL")
+    assert b"repeated" in lib.qaoa_last_error()
+    inst = _lib.NaesatInstance(40, 1, 3, var.ctypes.data, neg.ctypes.data)
+    assert lib.naesat_cost_table(ctypes.byref(inst), ctypes.c_void_p(1), None, None, None) == _lib_code("ERANGE")
+    g = np.array([0.1, float("nan")])
+    assert lib.qaoa_evolve(20, ctypes.c_void_p(1), 10, 2, g.ctypes.data, g.ctypes.data, 0, 0, ctypes.c_void_p(1),
+                           None, None, None) == _lib_code("EINVAL")
+    assert lib.qaoa_evolve(20, ctypes.c_void_p(1), 10, 1, g.ctypes.data, g.ctypes.data, 9, 0, ctypes.c_void_p(1),
+                           None, None, None) == _lib_code("EINVAL")
+    assert lib.qaoa_grad(20, ctypes.c_void_p(1), 10, 0, None, None, 0, 0, ctypes.c_void_p(1), ctypes.c_void_p(1),
+                         None, None, None, None) == _lib_code("EINVAL")
