@@ -100,14 +100,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(n: int, p: int, plan, es: int):
-    """Minimal HBM bytes each pass kind must move per evolution (2^n amplitudes):
-    low pass: read psi + write psi + read C (the first layer writes only); high
-    pass: read + write psi, plus C in the pass that reduces p_succ."""
+def algorithmic_bytes(n: int, p: int, dtype: str):
+    """Minimal HBM bytes each launch of the evolution must move, from the
+    library's own launch schedule: every pass reads and writes the state once;
+    the first pass of layer 0 only writes it (|+> comes from the phase table);
+    a pass that applies a phase reads the cost table once, and so does the last
+    pass (p_succ needs C).  Returns per-kind byte totals and launch counts."""
+    from paper_2401_02852_gb300 import api
+
+    es = 8 if dtype == "c64" else 16
     N = 2 ** n
-    low = N * ((2 * es + 1) * (p - 1) + (es + 1))
-    high = N * (2 * es) * p * (len(plan) - 1) + N  # + C read in the reducing pass
-    return {"pass_low": low, "pass_high": high, "launches": {"pass_low": p, "pass_high": p * (len(plan) - 1)}}
+    seq = api.pass_schedule(n, p, dtype)
+    out = {"pass_low": 0, "pass_high": 0, "launches": {"pass_low": 0, "pass_high": 0}}
+    for i, (pi, _, mode) in enumerate(seq):
+        kind = "pass_low" if pi == 0 else "pass_high"
+        if mode == 0:
+            b = N * (es + 1)
+        else:
+            b = N * 2 * es + (N if (mode == 2 or i + 1 == len(seq)) else 0)
+        out[kind] += b
+        out["launches"][kind] += 1
+    return out
 
 
 def measured_peak():
@@ -240,7 +253,7 @@ def run_native(args, ws, rank, local):
     # roofline of the dominant kernel from the live per-launch events
     kinds = prof.stats
     dom = max(kinds, key=lambda k: kinds[k][1])
-    alg = algorithmic_bytes(n, p, plan, es)
+    alg = algorithmic_bytes(n, p, dtype)
     peak, peak_src = measured_peak()
     roof = None
     if dom in ("pass_low", "pass_high"):

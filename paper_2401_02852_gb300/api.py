@@ -193,6 +193,16 @@ def plan(n: int, dtype="c64"):
     return [(lo[i], bits[i], row[i]) for i in range(k)]
 
 
+def pass_schedule(n: int, p: int, dtype="c64"):
+    """Launch sequence of an evolution: list of (pass index, layer, mode)."""
+    cap = max(1, p * 8 + 1)
+    idx = (ctypes.c_int * cap)()
+    lay = (ctypes.c_int * cap)()
+    mod = (ctypes.c_int * cap)()
+    k = check(load().qaoa_pass_schedule(n, p, dtype_code(dtype), cap, idx, lay, mod))
+    return [(idx[i], lay[i], mod[i]) for i in range(k)]
+
+
 class Profiler:
     """Per-kernel CUDA-event timing of every library launch inside the block."""
 

@@ -13,7 +13,9 @@
 //   V = (t == 0 ? all_false : 0) | (t == hi_mask ? all_true : 0),
 // i.e. all literals false, or all true.  The 32 per-x counts are kept as
 // bit planes by a carry-save (Harley-Seal) adder over chunks of 16 clauses,
-// then transposed to bytes with 8x8 bit-matrix transposes.  The number of
+// then transposed to bytes with 8x8 bit-matrix transposes.  The clause records
+// sit in shared memory (one broadcast 16-byte load per clause) and each thread
+// counts two words per record load.  The number of
 // solutions (count 0) and the largest count come out of the same pass.
 #include <cuda_runtime.h>
 
@@ -42,17 +44,13 @@ __device__ __forceinline__ uint32_t violation_word(uint32_t xh, const ClauseRec 
     return (t == 0u ? r.all_false : 0u) | (t == r.hi_mask ? r.all_true : 0u);
 }
 
-// Counts violated clauses for the 32 assignments of word X; planes[q] holds bit q
-// of every count (q = 0..9, counts up to 1023).
-template <class Rec>
-__device__ __forceinline__ void count_word(uint32_t X, int m, const Rec &rec, uint32_t planes[10]) {
-    const uint32_t xh = X << 5;
+// Carry-save counter of the violated clauses of one 32-assignment word:
+// bit plane q holds bit q of every count (q = 0..9, counts up to 1023).
+struct WordCounter {
     uint32_t ones = 0, twos = 0, fours = 0, eights = 0;
     uint32_t up[6] = {0, 0, 0, 0, 0, 0};
-    for (int i0 = 0; i0 < m; i0 += 16) {
-        uint32_t v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = (i0 + j < m) ? violation_word(xh, rec(i0 + j)) : 0u;
+    // Adds 16 violation words (a Harley-Seal chunk).
+    __device__ __forceinline__ void add16(const uint32_t v[16]) {
         uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
         csa(twosA, ones, ones, v[0], v[1]);
         csa(twosB, ones, ones, v[2], v[3]);
@@ -77,12 +75,37 @@ __device__ __forceinline__ void count_word(uint32_t X, int m, const Rec &rec, ui
             carry = t;
         }
     }
-    planes[0] = ones;
-    planes[1] = twos;
-    planes[2] = fours;
-    planes[3] = eights;
+    __device__ __forceinline__ void planes(uint32_t p[10]) const {
+        p[0] = ones;
+        p[1] = twos;
+        p[2] = fours;
+        p[3] = eights;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) planes[4 + q] = up[q];
+        for (int q = 0; q < 6; ++q) p[4 + q] = up[q];
+    }
+};
+
+// Counts two words X0, X1 against the clause records in shared memory
+// (m16 = m rounded up to 16; the padding records are all zero, which are never
+// violated: t = 0 = hi_mask selects all_false | all_true = 0).
+__device__ __forceinline__ void count_words2(uint32_t X0, uint32_t X1, int m16, const uint4 *srec, uint32_t p0[10],
+                                             uint32_t p1[10]) {
+    const uint32_t xh0 = X0 << 5, xh1 = X1 << 5;
+    WordCounter c0, c1;
+    for (int i0 = 0; i0 < m16; i0 += 16) {
+        uint32_t v0[16], v1[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint4 r4 = srec[i0 + j];
+            const ClauseRec r{r4.x, r4.y, r4.z, r4.w};
+            v0[j] = violation_word(xh0, r);
+            v1[j] = violation_word(xh1, r);
+        }
+        c0.add16(v0);
+        c1.add16(v1);
+    }
+    c0.planes(p0);
+    c1.planes(p1);
 }
 
 // 8x8 bit transpose of a 64-bit word (byte j = row j, bit i = column i).
@@ -112,49 +135,58 @@ __device__ __forceinline__ void planes_to_bytes(const uint32_t planes[10], uint3
     }
 }
 
-template <class Rec>
-__device__ __forceinline__ void cost_table_body(int n, int m, const Rec &rec, uint8_t *cost,
+// Writes the 32 counts of word X (bytes) and folds its solution count and max.
+__device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t planes[10], uint8_t *cost,
+                                          unsigned long long &nsol, uint32_t &mx) {
+    const uint32_t valid = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
+    uint32_t bytes[8];
+    planes_to_bytes(planes, bytes);
+    uint32_t any = 0;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) any |= planes[q];
+    nsol += __popc(~any & valid);
+    const uint32_t over = (planes[8] | planes[9]) & valid;
+    uint32_t bm = 0;
+    if (n >= 5) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) bm = __vmaxu4(bm, bytes[q]);
+        bm = max(max(bm & 0xFF, (bm >> 8) & 0xFF), max((bm >> 16) & 0xFF, bm >> 24));
+    } else {
+        for (uint32_t b = 0; b < (1u << n); ++b) bm = max(bm, (bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+    }
+    if (over) {  // some count >= 256: take those lanes exactly
+        for (uint32_t b = 0; b < 32; ++b)
+            if ((over >> b) & 1u) {
+                uint32_t c = 0;
+                for (int q = 0; q < 10; ++q) c |= ((planes[q] >> b) & 1u) << q;
+                bm = max(bm, c);
+            }
+    }
+    mx = max(mx, bm);
+    if (n >= 5) {
+        uint4 *dst = reinterpret_cast<uint4 *>(cost + 32 * X);
+        dst[0] = make_uint4(bytes[0], bytes[1], bytes[2], bytes[3]);
+        dst[1] = make_uint4(bytes[4], bytes[5], bytes[6], bytes[7]);
+    } else {
+        for (uint32_t b = 0; b < (1u << n); ++b) cost[b] = (uint8_t)((bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+    }
+}
+
+// One table: each thread takes the word pair (X, X + half) over a grid-stride
+// loop, so every clause record loaded from shared memory serves 64 assignments.
+__device__ __forceinline__ void cost_table_body(int n, int m16, const uint4 *srec, uint8_t *cost,
                                                 unsigned long long *stats) {
     const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
-    const uint32_t valid = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
+    const uint64_t half = (words + 1) / 2;
     unsigned long long nsol = 0;
     uint32_t mx = 0;
-    for (uint64_t X = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; X < words;
+    for (uint64_t X = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; X < half;
          X += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t planes[10];
-        count_word((uint32_t)X, m, rec, planes);
-        uint32_t bytes[8];
-        planes_to_bytes(planes, bytes);
-        uint32_t any = 0;
-#pragma unroll
-        for (int q = 0; q < 10; ++q) any |= planes[q];
-        nsol += __popc(~any & valid);
-        // largest count among the valid lanes
-        const uint32_t over = (planes[8] | planes[9]) & valid;
-        uint32_t bm = 0;
-        if (n >= 5) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) bm = __vmaxu4(bm, bytes[q]);
-            bm = max(max(bm & 0xFF, (bm >> 8) & 0xFF), max((bm >> 16) & 0xFF, bm >> 24));
-        } else {
-            for (uint32_t b = 0; b < (1u << n); ++b) bm = max(bm, (bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
-        }
-        if (over) {  // some count >= 256: take those lanes exactly
-            for (uint32_t b = 0; b < 32; ++b)
-                if ((over >> b) & 1u) {
-                    uint32_t c = 0;
-                    for (int q = 0; q < 10; ++q) c |= ((planes[q] >> b) & 1u) << q;
-                    bm = max(bm, c);
-                }
-        }
-        mx = max(mx, bm);
-        if (n >= 5) {
-            uint4 *dst = reinterpret_cast<uint4 *>(cost + 32 * X);
-            dst[0] = make_uint4(bytes[0], bytes[1], bytes[2], bytes[3]);
-            dst[1] = make_uint4(bytes[4], bytes[5], bytes[6], bytes[7]);
-        } else {
-            for (uint32_t b = 0; b < (1u << n); ++b) cost[b] = (uint8_t)((bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
-        }
+        const uint64_t X1 = X + half;
+        uint32_t p0[10], p1[10];
+        count_words2((uint32_t)X, (uint32_t)(X1 < words ? X1 : X), m16, srec, p0, p1);
+        emit_word(n, X, p0, cost, nsol, mx);
+        if (X1 < words) emit_word(n, X1, p1, cost, nsol, mx);
     }
     // warp then block reduction, one atomic pair per block
 #pragma unroll
@@ -182,22 +214,18 @@ __device__ __forceinline__ void cost_table_body(int n, int m, const Rec &rec, ui
     }
 }
 
-struct ParamRec {
-    const CostParams *p;
-    __device__ __forceinline__ ClauseRec operator()(int i) const { return p->rec[i]; }
-};
-struct GlobalRec {
-    const ClauseRec *r;
-    __device__ __forceinline__ ClauseRec operator()(int i) const {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(r + i));
-        return ClauseRec{v.x, v.y, v.z, v.w};
-    }
-};
+constexpr int MAX_M16 = (QAOA_MAX_M + 15) / 16 * 16;
 
 __global__ void __launch_bounds__(CT_THREADS) cost_table_kernel(const __grid_constant__ CostParams prm, uint8_t *cost,
                                                                 unsigned long long *stats) {
-    ParamRec rec{&prm};
-    cost_table_body(prm.n, prm.m, rec, cost, stats);
+    __shared__ uint4 srec[MAX_M16];
+    const int m16 = (prm.m + 15) / 16 * 16;
+    for (int i = threadIdx.x; i < m16; i += CT_THREADS) {
+        const ClauseRec r = i < prm.m ? prm.rec[i] : ClauseRec{0, 0, 0, 0};
+        srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
+    }
+    __syncthreads();
+    cost_table_body(prm.n, m16, srec, cost, stats);
 }
 
 // Batched tables.  With ns == nullptr every instance has n qubits and its table
@@ -207,11 +235,19 @@ __global__ void __launch_bounds__(CT_THREADS) cost_table_batch_kernel(int n, con
                                                                       const ClauseRec *recs, const int *ms,
                                                                       int m_stride, uint8_t *costs,
                                                                       unsigned long long *stats) {
+    __shared__ uint4 srec[MAX_M16];
     const int inst = blockIdx.y;
-    GlobalRec rec{recs + (size_t)inst * m_stride};
+    const int m = ms[inst];
+    const int m16 = (m + 15) / 16 * 16;
+    const ClauseRec *g = recs + (size_t)inst * m_stride;
+    for (int i = threadIdx.x; i < m16; i += CT_THREADS) {
+        const ClauseRec r = i < m ? g[i] : ClauseRec{0, 0, 0, 0};
+        srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
+    }
+    __syncthreads();
     const int ni = ns ? ns[inst] : n;
     uint8_t *dst = ns ? costs + offs[inst] : costs + ((size_t)inst << n);
-    cost_table_body(ni, ms[inst], rec, dst, stats + 2 * inst);
+    cost_table_body(ni, m16, srec, dst, stats + 2 * inst);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,7 +303,7 @@ int encode_instance(const naesat_instance *inst, ClauseRec *out) {
 static int grid_for(uint64_t words, int batch) {
     DeviceInfo di;
     if (device_info(&di)) return -1;
-    const uint64_t need = (words + CT_THREADS - 1) / CT_THREADS;
+    const uint64_t need = ((words + 1) / 2 + CT_THREADS - 1) / CT_THREADS;
     uint64_t cap = (uint64_t)di.sms * 8 * 4;
     cap = cap / (uint64_t)batch + 1;
     return (int)(need < cap ? need : cap);

@@ -30,8 +30,9 @@ struct PassArgs {
     double *partials;          // [batch][gridDim.x][2] when reduce
     int n, row, lo, m;
     uint32_t active;           // tile bits to butterfly
-    int init, reduce, unit_a;
-    R A, B;
+    int reduce;
+    int ua1, ua2;              // butterfly forms of the two layers (fused: l, l+1)
+    R A1, B1, A2, B2;
     uint64_t tiles;            // tiles per instance
 };
 
@@ -40,12 +41,80 @@ struct PhaseTab {
     typename Cx<R>::V t[NT];
 };
 
-template <typename R, bool LOW, bool PHASE, bool UA>
+// Pass modes.  INIT: the first pass of layer 0 (the state is |+>, the table
+// holds the amplitude times the phase).  PLAIN: butterflies of one layer.
+// FUSED: butterflies of layer l on the pass's qubits, the phase of layer l+1,
+// then the butterflies of layer l+1 on the same qubits (the pass is the last
+// of layer l and the first of layer l+1; the qubit factors commute, so the
+// group order alternates between layers).
+// The rounds of one layer from the load mapping (8) to the store mapping (LC)...
+template <typename G, bool LOW, bool UA>
+__device__ __forceinline__ void rounds_up(typename G::V *v, typename G::V *tile, uint32_t active, typename G::Real A,
+                                          typename G::Real B) {
+    constexpr int T = G::T, LC = LOW ? G::LC_LOW : G::LC_HIGH;
+    reg_butterflies<G, UA, 8, T>(v, active, A, B);
+    if (LOW) {
+        exchange<G, 8, 0>(v, tile);
+        reg_butterflies<G, UA, 0, T>(v, active, A, B);
+        exchange<G, 0, LC>(v, tile);
+    } else {
+        exchange<G, 8, LC>(v, tile);
+    }
+    reg_butterflies<G, UA, LC, 8>(v, active, A, B);
+}
+
+// ... and back from LC to 8 (same qubits, reverse round order).
+template <typename G, bool LOW, bool UA>
+__device__ __forceinline__ void rounds_down(typename G::V *v, typename G::V *tile, uint32_t active,
+                                            typename G::Real A, typename G::Real B) {
+    constexpr int T = G::T, LC = LOW ? G::LC_LOW : G::LC_HIGH;
+    reg_butterflies<G, UA, LC, 8>(v, active, A, B);
+    if (LOW) {
+        exchange<G, LC, 0>(v, tile);
+        reg_butterflies<G, UA, 0, T>(v, active, A, B);
+        exchange<G, 0, 8>(v, tile);
+    } else {
+        exchange<G, LC, 8>(v, tile);
+    }
+    reg_butterflies<G, UA, 8, T>(v, active, A, B);
+}
+
+// Stores the tile (thread pointer + r * stride), fusing the p_succ / norm
+// partials and the adjoint seed P psi when this is the evolution's last pass.
+template <typename R>
+__device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename Cx<R>::V *sp, const uint8_t *sc,
+                                           typename Cx<R>::V *sa, uint64_t stride, bool reduce, double acc[2]) {
+    using V = typename Cx<R>::V;
+    constexpr int NR = Cx<R>::NR;
+    asm volatile("" : "+l"(sp));  // keep the store addresses out of the load phase
+    R ps = 0, nm = 0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        sp[r * stride] = v[r];
+        if (reduce) {
+            const R w = v[r].x * v[r].x + v[r].y * v[r].y;
+            nm += w;
+            const bool sol = sc[r * stride] == 0;
+            if (sol) ps += w;
+            if (sa) {
+                V z;
+                z.x = sol ? v[r].x : R(0);
+                z.y = sol ? v[r].y : R(0);
+                sa[r * stride] = z;
+            }
+        }
+    }
+    acc[0] += (double)ps;
+    acc[1] += (double)nm;
+}
+
+template <typename R, bool LOW, int MODE>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
                                            typename Cx<R>::V *tile) {
-    using V = typename Cx<R>::V;
-    constexpr int T = Cx<R>::T, RB = Cx<R>::RB, NR = 1 << RB;
-    constexpr int LC = LOW ? Cx<R>::LC_LOW : Cx<R>::LC_HIGH;
+    using G = Cx<R>;
+    using V = typename G::V;
+    constexpr int T = G::T, NR = G::NR;
+    constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
     const uint32_t tid = threadIdx.x;
     const size_t inst = blockIdx.y;
     V *st = a.state + (inst << a.n);
@@ -53,63 +122,40 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     const uint8_t *cs = a.cost + (inst << a.n);
     // Every tile address is thread pointer + r * stride (the plan keeps the row
     // width at 4 bits in high passes, so the register bits are all strided).
-    const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<Cx<R>, 8>(tid, 0), a.row, a.lo);
+    const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<G, 8>(tid, 0), a.row, a.lo);
     const uint64_t ld_s = LOW ? 256u : (1ull << (a.lo + 8 - a.row));
-    const uint64_t st_t = elem_offset(tile_elem<Cx<R>, LC>(tid, 0), a.row, a.lo);
+    const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
     const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     for (uint64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
         const uint64_t base = tile_base(t, a.row, a.lo, T);
         V v[NR];
-        // load (mapping 8: coalesced), phase fused
-        {
+        {  // load (mapping 8: coalesced); layer 0 starts from the table
             const V *lp = st + base + ld_t;
             const uint8_t *lc = cs + base + ld_t;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                if (PHASE && a.init) {
-                    v[r] = stab[lc[r * ld_s]];
-                } else {
-                    v[r] = lp[r * ld_s];
-                    if (PHASE) v[r] = cmul(v[r], stab[lc[r * ld_s]]);
-                }
-            }
+            for (int r = 0; r < NR; ++r) v[r] = MODE == MODE_INIT ? stab[lc[r * ld_s]] : lp[r * ld_s];
         }
-        reg_butterflies<Cx<R>, UA, 8, T>(v, a.active, a.A, a.B);
-        if (LOW) {
-            exchange<Cx<R>, 8, 0>(v, tile);
-            reg_butterflies<Cx<R>, UA, 0, T>(v, a.active, a.A, a.B);
-            exchange<Cx<R>, 0, LC>(v, tile);
-        } else {
-            exchange<Cx<R>, 8, LC>(v, tile);
-        }
-        reg_butterflies<Cx<R>, UA, LC, 8>(v, a.active, a.A, a.B);
-        // store (mapping LC: coalesced), reduction fused
-        R ps = 0, nm = 0;
-        {
-            V *sp = st + base + st_t;
-            asm volatile("" : "+l"(sp));  // keep the store addresses out of the load phase
-            const uint8_t *sc = cs + base + st_t;
-            V *sa = adj ? adj + base + st_t : nullptr;
+        if (a.ua1)
+            rounds_up<G, LOW, true>(v, tile, a.active, a.A1, a.B1);
+        else
+            rounds_up<G, LOW, false>(v, tile, a.active, a.A1, a.B1);
+        if (MODE == MODE_FUSED) {
+            {  // phase of layer l+1 in the LC mapping
+                const uint8_t *pc = cs + base + st_t;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                sp[r * st_s] = v[r];
-                if (a.reduce) {
-                    const R w = v[r].x * v[r].x + v[r].y * v[r].y;
-                    nm += w;
-                    const bool sol = sc[r * st_s] == 0;
-                    if (sol) ps += w;
-                    if (sa) {
-                        V z;
-                        z.x = sol ? v[r].x : R(0);
-                        z.y = sol ? v[r].y : R(0);
-                        sa[r * st_s] = z;
-                    }
-                }
+                for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[pc[r * st_s]]);
             }
+            if (a.ua2)
+                rounds_down<G, LOW, true>(v, tile, a.active, a.A2, a.B2);
+            else
+                rounds_down<G, LOW, false>(v, tile, a.active, a.A2, a.B2);
+            store_tile<R>(v, st + base + ld_t, cs + base + ld_t, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce,
+                          acc);
+        } else {
+            store_tile<R>(v, st + base + st_t, cs + base + st_t, adj ? adj + base + st_t : nullptr, st_s, a.reduce,
+                          acc);
         }
-        acc[0] += (double)ps;
-        acc[1] += (double)nm;
     }
     if (a.reduce) {
         block_sum<2>(acc);
@@ -121,14 +167,14 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     }
 }
 
-template <typename R, bool LOW, bool PHASE, int NT>
+template <typename R, bool LOW, int MODE, int NT>
 __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                      const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
     V *stab = tile + (1 << Cx<R>::T);
-    if (PHASE) {  // 256 entries at least: any uint8 cost indexes inside the table
+    if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
             V z;
             z.x = z.y = 0;
@@ -136,10 +182,7 @@ __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ Pas
         }
         __syncthreads();
     }
-    if (a.unit_a)
-        pass_tiles<R, LOW, PHASE, true>(a, stab, tile);
-    else
-        pass_tiles<R, LOW, PHASE, false>(a, stab, tile);
+    pass_tiles<R, LOW, MODE>(a, stab, tile);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -328,34 +371,17 @@ template <typename R>
 struct PassKernels {
     using Full = PhaseTab<R, MAX_TABLE>;
     using None = PhaseTab<R, 1>;
-    int blocks_per_sm[2][2] = {{0, 0}, {0, 0}};  // [low][phase]
     cudaError_t init() {
         const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(pass_kernel<R, true, true, MAX_TABLE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-            return e;
-        if ((e = cudaFuncSetAttribute(pass_kernel<R, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-            return e;
-        if ((e = cudaFuncSetAttribute(pass_kernel<R, false, true, MAX_TABLE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-            return e;
-        if ((e = cudaFuncSetAttribute(pass_kernel<R, false, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      big)))
-            return e;
-        const size_t s_phase = pass_smem<R>(true, 255), s_plain = pass_smem<R>(false, 0);
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[1][1],
-                                                               pass_kernel<R, true, true, MAX_TABLE>, PT, s_phase)))
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[1][0], pass_kernel<R, true, false, 1>, PT,
-                                                               s_plain)))
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[0][1],
-                                                               pass_kernel<R, false, true, MAX_TABLE>, PT, s_phase)))
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[0][0], pass_kernel<R, false, false, 1>,
-                                                               PT, s_plain)))
-            return e;
+        const void *ks[] = {(const void *)pass_kernel<R, true, MODE_INIT, MAX_TABLE>,
+                            (const void *)pass_kernel<R, true, MODE_PLAIN, 1>,
+                            (const void *)pass_kernel<R, false, MODE_PLAIN, 1>,
+                            (const void *)pass_kernel<R, true, MODE_FUSED, MAX_TABLE>,
+                            (const void *)pass_kernel<R, false, MODE_FUSED, MAX_TABLE>};
+        for (const void *k : ks) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+            if (e != cudaSuccess) return e;
+        }
         return cudaSuccess;
     }
 };
@@ -392,6 +418,19 @@ int pass_grid_x(int dtype, int n, int batch) {
 }
 
 template <typename R>
+static void fill_table(typename PassKernels<R>::Full *tab, const EvolveReq &r, int l, int sign) {
+    std::vector<double> re(r.m + 1), im(r.m + 1);
+    const LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+    double scale = std::pow(k.sigma, r.n);
+    if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
+    phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());
+    for (int c = 0; c <= r.m; ++c) {
+        tab->t[c].x = (R)re[c];
+        tab->t[c].y = (R)im[c];
+    }
+}
+
+template <typename R>
 static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStream_t stream) {
     using V = typename Cx<R>::V;
     PassKernels<R> *pk = nullptr;
@@ -403,67 +442,68 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
     constexpr int T = Cx<R>::T;
     const int sign = (r.flags & QAOA_MIXER_RX2B) ? -1 : 1;
     const bool want = r.d_result != nullptr;
-    const int p_eff = r.p > 0 ? r.p : 1;
-    std::vector<double> re(r.m + 1), im(r.m + 1);
     // The phase table is large: keep it off the stack.
     std::vector<char> tbuf(sizeof(typename PassKernels<R>::Full));
     auto *tab = reinterpret_cast<typename PassKernels<R>::Full *>(tbuf.data());
     typename PassKernels<R>::None none{};
-    const dim3 block(PT);
-    for (int l = 0; l < p_eff; ++l) {
-        LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
-        double scale = std::pow(k.sigma, r.n);
-        if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
-        phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());
-        for (int c = 0; c <= r.m; ++c) {
-            tab->t[c].x = (R)re[c];
-            tab->t[c].y = (R)im[c];
+    const std::vector<Launch> seq = make_schedule(pl.n_passes, r.p);
+    const dim3 block(PT), grid(gx, r.batch);
+    for (size_t i = 0; i < seq.size(); ++i) {
+        const Launch &L = seq[i];
+        const Pass &ps = pl.pass[L.pass];
+        const bool low = L.pass == 0;
+        PassArgs<R> a;
+        a.state = reinterpret_cast<V *>(r.state);
+        a.cost = r.cost;
+        a.partials = d_partials;
+        a.n = r.n;
+        a.m = r.m;
+        if (low) {  // the whole tile is one contiguous row
+            a.row = T;
+            a.lo = T;
+            a.active = r.p > 0 ? ((1u << T) - 1u) : 0u;
+        } else {
+            a.row = ps.row;
+            a.lo = ps.lo;
+            a.active = ((1u << ps.bits) - 1u) << (T - ps.bits);
         }
-        const int np = r.p > 0 ? pl.n_passes : 1;
-        for (int i = 0; i < np; ++i) {
-            const Pass &ps = pl.pass[i];
-            PassArgs<R> a;
-            a.state = reinterpret_cast<V *>(r.state);
-            a.cost = r.cost;
-            a.partials = d_partials;
-            a.n = r.n;
-            a.m = r.m;
-            if (i == 0) {  // low pass: the whole tile is one contiguous row
-                a.row = T;
-                a.lo = T;
-                a.active = r.p > 0 ? ((1u << T) - 1u) : 0u;
-            } else {
-                a.row = ps.row;
-                a.lo = ps.lo;
-                a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
-            }
-            a.init = (l == 0 && i == 0) ? 1 : 0;
-            const bool last = (l == p_eff - 1 && i == np - 1);
-            a.reduce = (last && (want || r.adj)) ? 1 : 0;
-            a.adj = (last && r.adj) ? reinterpret_cast<V *>(r.adj) : nullptr;
-            a.unit_a = k.unit_a ? 1 : 0;
-            a.A = (R)k.A;
-            a.B = (R)k.B;
-            a.tiles = 1ull << (r.n - T);
-            const dim3 grid(gx, r.batch);
-            if (i == 0) {
-                profile_before(K_PASS_LOW, stream);
-                pass_kernel<R, true, true, MAX_TABLE>
-                    <<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
-                rc = profile_after(K_PASS_LOW, stream);
-            } else {
-                profile_before(K_PASS_HIGH, stream);
-                pass_kernel<R, false, false, 1><<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
-                rc = profile_after(K_PASS_HIGH, stream);
-            }
-            if (rc) return rc;
+        const bool last = i + 1 == seq.size();
+        a.reduce = (last && (want || r.adj)) ? 1 : 0;
+        a.adj = (last && r.adj) ? reinterpret_cast<V *>(r.adj) : nullptr;
+        const LayerCoef k1 = r.p > 0 ? layer_coef(r.beta[L.la], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+        a.ua1 = k1.unit_a;
+        a.A1 = (R)k1.A;
+        a.B1 = (R)k1.B;
+        a.ua2 = 1;
+        a.A2 = a.B2 = (R)0;
+        if (L.mode == MODE_FUSED) {
+            const LayerCoef k2 = layer_coef(r.beta[L.la + 1], sign);
+            a.ua2 = k2.unit_a;
+            a.A2 = (R)k2.A;
+            a.B2 = (R)k2.B;
         }
+        a.tiles = 1ull << (r.n - T);
+        const int kind = low ? K_PASS_LOW : K_PASS_HIGH;
+        profile_before(kind, stream);
+        if (L.mode == MODE_INIT) {
+            fill_table<R>(tab, r, 0, sign);
+            pass_kernel<R, true, MODE_INIT, MAX_TABLE><<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+        } else if (L.mode == MODE_FUSED) {
+            fill_table<R>(tab, r, L.la + 1, sign);
+            if (low)
+                pass_kernel<R, true, MODE_FUSED, MAX_TABLE><<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            else
+                pass_kernel<R, false, MODE_FUSED, MAX_TABLE><<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+        } else {
+            if (low)
+                pass_kernel<R, true, MODE_PLAIN, 1><<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            else
+                pass_kernel<R, false, MODE_PLAIN, 1><<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+        }
+        rc = profile_after(kind, stream);
+        if (rc) return rc;
     }
-    if (want) {
-        profile_before(K_REDUCE, stream);
-        reduce_partials_kernel<<<r.batch, PT, 0, stream>>>(d_partials, gx, 2, r.d_result);
-        rc = profile_after(K_REDUCE, stream);
-    }
+    if (want) rc = launch_reduce(d_partials, r.batch, gx, 2, r.d_result, stream);
     return rc;
 }
 

@@ -89,6 +89,17 @@ int make_plan(int n, int dtype, Plan *plan);
 // Plan for a tile of 2^T amplitudes and high groups of at most gmax bits.
 int make_plan_geo(int n, int T, int gmax, Plan *plan);
 
+// One launch of the forward evolution: pass `pass` of the plan for layer `la`.
+// Modes: 0 = first pass of layer 0 (state |+> generated from the phase table),
+// 1 = butterflies of one layer, 2 = butterflies of layer la, the phase of
+// layer la + 1 and the butterflies of layer la + 1 (the group order alternates
+// between layers so the last pass of a layer and the first of the next fuse).
+struct Launch {
+    int pass, la, mode;
+};
+enum PassMode { MODE_INIT = 0, MODE_PLAIN = 1, MODE_FUSED = 2 };
+std::vector<Launch> make_schedule(int n_passes, int p);
+
 // ---------------------------------------------------------------------------
 // Host-side per-layer coefficients.  One mixer layer is
 //   prod_j [c I + i S X_j] = sigma^n prod_j [A I + i B X_j]

@@ -178,6 +178,25 @@ int make_plan(int n, int dtype, Plan *plan) {
     return dtype == QAOA_C64 ? make_plan_geo(n, T_C64, G_MAX_C64, plan) : make_plan_geo(n, T_C128, G_MAX_C128, plan);
 }
 
+std::vector<Launch> make_schedule(int n_passes, int p) {
+    std::vector<Launch> out;
+    if (p == 0) {
+        out.push_back({0, 0, MODE_INIT});
+        return out;
+    }
+    for (int l = 0; l < p; ++l) {
+        for (int j = 0; j < n_passes; ++j) {
+            if (l > 0 && j == 0) continue;  // fused into the previous layer's last pass
+            const int ps = (l % 2 == 0) ? j : n_passes - 1 - j;
+            int mode = MODE_PLAIN;
+            if (l == 0 && j == 0) mode = MODE_INIT;
+            if (j == n_passes - 1 && l + 1 < p) mode = MODE_FUSED;
+            out.push_back({ps, l, mode});
+        }
+    }
+    return out;
+}
+
 LayerCoef layer_coef(double beta, int sign) {
     const double c = std::cos(beta), sn = std::sin(beta);
     const double S = sign * sn;  // butterfly: a' = c a + i S b, b' = i S a + c b
@@ -225,6 +244,20 @@ int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits) {
         if (row_bits) row_bits[i] = pl.pass[i].row;
     }
     return pl.n_passes;
+}
+
+int qaoa_pass_schedule(int n, int p, int dtype, int max_launches, int *pass_index, int *layer, int *mode) {
+    Plan pl;
+    if (p < 0) return set_error(QAOA_EINVAL, "p=%d", p);
+    int rc = make_plan(n, dtype, &pl);
+    if (rc) return rc;
+    const std::vector<Launch> seq = make_schedule(pl.n_passes, p);
+    for (size_t i = 0; i < seq.size() && (int)i < max_launches; ++i) {
+        if (pass_index) pass_index[i] = seq[i].pass;
+        if (layer) layer[i] = seq[i].la;
+        if (mode) mode[i] = seq[i].mode;
+    }
+    return (int)seq.size();
 }
 
 int qaoa_profile_enable(int on) {

@@ -96,3 +96,50 @@ def test_argument_validation_precedes_device_work(lib):
                            None, None, None) == _lib_code("EINVAL")
     assert lib.qaoa_grad(20, ctypes.c_void_p(1), 10, 0, None, None, 0, 0, ctypes.c_void_p(1), ctypes.c_void_p(1),
                          None, None, None, None) == _lib_code("EINVAL")
+
+
+def _schedule(lib, n, p, dtype):
+    cap = 8 * p + 8
+    idx, lay, mod = (ctypes.c_int * cap)(), (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+    k = lib.qaoa_pass_schedule(n, p, dtype, cap, idx, lay, mod)
+    return [(idx[i], lay[i], mod[i]) for i in range(k)]
+
+
+@pytest.mark.parametrize("dtype,T", [(0, 13), (1, 12)])
+@pytest.mark.parametrize("p", [0, 1, 2, 5, 10])
+def test_schedule_applies_each_layer_in_order(lib, dtype, T, p):
+    """Replays the launch sequence symbolically: every layer applies its phase
+    once, then mixes every qubit exactly once, before the next layer's phase
+    (the layer product of the QAOA output state)."""
+    for n in (T + 1, 22, 30, 32):
+        _, passes = _plan(lib, n, dtype)
+        G = T - passes[1][2]
+
+        def qubits(i):
+            if i == 0:
+                return list(range(T))
+            lo, bits, _ = passes[i]
+            return list(range(lo + G - bits, lo + G))
+
+        events = []
+        for pi, l, mode in _schedule(lib, n, p, dtype):
+            if mode == 0:
+                events.append(("phase", 0, None))
+            if p > 0:
+                events += [("mix", l, q) for q in qubits(pi)]
+            if mode == 2:
+                events.append(("phase", l + 1, None))
+                events += [("mix", l + 1, q) for q in qubits(pi)]
+        if p == 0:
+            assert events == [("phase", 0, None)]
+            continue
+        assert len(_schedule(lib, n, p, dtype)) == p * (len(passes) - 1) + 1
+        layer, seen = -1, None
+        for kind, l, q in events:
+            if kind == "phase":
+                assert l == layer + 1 and (seen is None or sorted(seen) == list(range(n)))
+                layer, seen = l, []
+            else:
+                assert l == layer and q not in seen
+                seen.append(q)
+        assert layer == p - 1 and sorted(seen) == list(range(n))

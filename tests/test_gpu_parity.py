@@ -34,6 +34,7 @@ def _inst(tag, n, k, m, idx=0):
 
 
 def _sat_inst(tag, n, k, m):
+    """First satisfiable draw (k = 1 clauses are always violated, so those cases use m = 0)."""
     for idx in range(2000):
         inst = _inst(tag, n, k, m, idx)
         cost, sol, mx = oracle.cost_table(n, inst.var, inst.neg)
@@ -127,7 +128,7 @@ def _angles(p, kind):
     return g, b
 
 
-EVOLVE_CASES = [(1, 1, 1, 2), (2, 2, 3, 1), (5, 3, 10, 3), (12, 3, 24, 5), (13, 3, 26, 3), (14, 5, 112, 2),
+EVOLVE_CASES = [(1, 1, 0, 2), (2, 2, 3, 1), (5, 3, 10, 3), (12, 3, 24, 5), (13, 3, 26, 3), (14, 5, 112, 2),
                 (16, 5, 128, 4), (20, 5, 160, 3), (22, 4, 100, 2)]
 
 
