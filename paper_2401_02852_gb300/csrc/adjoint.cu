@@ -137,20 +137,21 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
         R gterm = 0;
         {
             V *pp = psi + base + st_t;
-            asm volatile("" : "+l"(pp));  // keep the store addresses out of the load phase
+            uint64_t ss = st_s;
+            asm volatile("" : "+l"(pp), "+l"(ss));  // keep the store addresses out of the load phase
             V *pl = lam + base + st_t;
             const uint8_t *pc = cs + base + st_t;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 if (LOW) {  // all of M_l undone: phase term, then D_l^dagger
-                    const int cst = pc[r * st_s];
+                    const int cst = pc[r * ss];
                     gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
                     const V ph = stab[cst];
                     vp[r] = cmul(vp[r], ph);
                     vl[r] = cmul(vl[r], ph);
                 }
-                pp[r * st_s] = vp[r];
-                pl[r * st_s] = vl[r];
+                pp[r * ss] = vp[r];
+                pl[r * ss] = vl[r];
             }
         }
         acc[0] += (double)term;

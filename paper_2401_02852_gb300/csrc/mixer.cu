@@ -86,7 +86,9 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
                                            typename Cx<R>::V *sa, uint64_t stride, bool reduce, double acc[2]) {
     using V = typename Cx<R>::V;
     constexpr int NR = Cx<R>::NR;
-    asm volatile("" : "+l"(sp));  // keep the store addresses out of the load phase
+    // Opaque to the compiler: otherwise it keeps the load phase's 32 offsets
+    // r * stride live across the whole tile to reuse them here.
+    asm volatile("" : "+l"(sp), "+l"(stride));
     R ps = 0, nm = 0;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -108,7 +110,7 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
     acc[1] += (double)nm;
 }
 
-template <typename R, bool LOW, int MODE>
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
                                            typename Cx<R>::V *tile) {
     using G = Cx<R>;
@@ -136,20 +138,16 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = MODE == MODE_INIT ? stab[lc[r * ld_s]] : lp[r * ld_s];
         }
-        if (a.ua1)
-            rounds_up<G, LOW, true>(v, tile, a.active, a.A1, a.B1);
-        else
-            rounds_up<G, LOW, false>(v, tile, a.active, a.A1, a.B1);
+        rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1);
         if (MODE == MODE_FUSED) {
             {  // phase of layer l+1 in the LC mapping
                 const uint8_t *pc = cs + base + st_t;
+                uint64_t ps = st_s;
+                asm volatile("" : "+l"(pc), "+l"(ps));  // not hoisted above the rounds of layer l
 #pragma unroll
-                for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[pc[r * st_s]]);
+                for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[pc[r * ps]]);
             }
-            if (a.ua2)
-                rounds_down<G, LOW, true>(v, tile, a.active, a.A2, a.B2);
-            else
-                rounds_down<G, LOW, false>(v, tile, a.active, a.A2, a.B2);
+            rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2);
             store_tile<R>(v, st + base + ld_t, cs + base + ld_t, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce,
                           acc);
         } else {
@@ -167,7 +165,9 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     }
 }
 
-template <typename R, bool LOW, int MODE, int NT>
+// UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
+// chosen on the host per layer.
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT>
 __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                      const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ Pas
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE>(a, stab, tile);
+    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, tile);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -371,13 +371,33 @@ template <typename R>
 struct PassKernels {
     using Full = PhaseTab<R, MAX_TABLE>;
     using None = PhaseTab<R, 1>;
+    using KFull = void (*)(PassArgs<R>, Full);
+    using KNone = void (*)(PassArgs<R>, None);
+    // [ua1] for init / plain, [low][ua1][ua2] for fused
+    KFull init_k[2] = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE>,
+                       pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE>};
+    KNone plain_low[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1>,
+                          pass_kernel<R, true, MODE_PLAIN, true, false, 1>};
+    KNone plain_high[2] = {pass_kernel<R, false, MODE_PLAIN, false, false, 1>,
+                           pass_kernel<R, false, MODE_PLAIN, true, false, 1>};
+    KFull fused[2][2][2] = {{{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE>,
+                              pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE>},
+                             {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE>,
+                              pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE>}},
+                            {{pass_kernel<R, true, MODE_FUSED, false, false, MAX_TABLE>,
+                              pass_kernel<R, true, MODE_FUSED, false, true, MAX_TABLE>},
+                             {pass_kernel<R, true, MODE_FUSED, true, false, MAX_TABLE>,
+                              pass_kernel<R, true, MODE_FUSED, true, true, MAX_TABLE>}}};
     cudaError_t init() {
         const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
-        const void *ks[] = {(const void *)pass_kernel<R, true, MODE_INIT, MAX_TABLE>,
-                            (const void *)pass_kernel<R, true, MODE_PLAIN, 1>,
-                            (const void *)pass_kernel<R, false, MODE_PLAIN, 1>,
-                            (const void *)pass_kernel<R, true, MODE_FUSED, MAX_TABLE>,
-                            (const void *)pass_kernel<R, false, MODE_FUSED, MAX_TABLE>};
+        std::vector<const void *> ks;
+        for (int i = 0; i < 2; ++i) {
+            ks.push_back((const void *)init_k[i]);
+            ks.push_back((const void *)plain_low[i]);
+            ks.push_back((const void *)plain_high[i]);
+            for (int j = 0; j < 2; ++j)
+                for (int k = 0; k < 2; ++k) ks.push_back((const void *)fused[i][j][k]);
+        }
         for (const void *k : ks) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
             if (e != cudaSuccess) return e;
@@ -485,20 +505,17 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         a.tiles = 1ull << (r.n - T);
         const int kind = low ? K_PASS_LOW : K_PASS_HIGH;
         profile_before(kind, stream);
+        const int u1 = a.ua1 ? 1 : 0, u2 = a.ua2 ? 1 : 0;
         if (L.mode == MODE_INIT) {
             fill_table<R>(tab, r, 0, sign);
-            pass_kernel<R, true, MODE_INIT, MAX_TABLE><<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            pk->init_k[u1]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
         } else if (L.mode == MODE_FUSED) {
             fill_table<R>(tab, r, L.la + 1, sign);
-            if (low)
-                pass_kernel<R, true, MODE_FUSED, MAX_TABLE><<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
-            else
-                pass_kernel<R, false, MODE_FUSED, MAX_TABLE><<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            pk->fused[low ? 1 : 0][u1][u2]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+        } else if (low) {
+            pk->plain_low[u1]<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
         } else {
-            if (low)
-                pass_kernel<R, true, MODE_PLAIN, 1><<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
-            else
-                pass_kernel<R, false, MODE_PLAIN, 1><<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            pk->plain_high[u1]<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
         }
         rc = profile_after(kind, stream);
         if (rc) return rc;

@@ -125,16 +125,23 @@ __device__ __forceinline__ void reg_butterflies(typename G::V *v, uint32_t mask,
 }
 
 // Re-distribute the tile from mapping FROM to mapping TO through shared memory.
+// The swizzle is linear over XOR and the thread and register parts of a tile
+// element have disjoint bits, so swz(u) = swz(thread part) ^ swz(r << LO), the
+// second term a compile-time constant: one LOP3 per access.  The thread parts
+// pass through an opaque asm so that the compiler recomputes addresses per
+// tile instead of hoisting (and spilling) all of them out of the tile loop.
 template <typename G, int FROM, int TO>
 __device__ __forceinline__ void exchange(typename G::V *v, typename G::V *tile) {
     constexpr int NR = G::NR;
     const uint32_t tid = threadIdx.x;
+    uint32_t bf = G::swz(tile_elem<G, FROM>(tid, 0)), bt = G::swz(tile_elem<G, TO>(tid, 0));
+    asm volatile("" : "+r"(bf), "+r"(bt));
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) tile[G::swz(tile_elem<G, FROM>(tid, r))] = v[r];
+    for (int r = 0; r < NR; ++r) tile[bf ^ G::swz((uint32_t)r << FROM)] = v[r];
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = tile[G::swz(tile_elem<G, TO>(tid, r))];
+    for (int r = 0; r < NR; ++r) v[r] = tile[bt ^ G::swz((uint32_t)r << TO)];
 }
 
 // FP64 block reduction of NV values per thread; thread 0 gets the sums.

@@ -228,7 +228,7 @@ def test_global_flip_symmetry_of_gpu_state():
 @pytest.mark.parametrize("n,dtype", [(9, "c128"), (9, "c64"), (14, "c128"), (15, "c64"), (18, "c128"), (18, "c64")])
 @pytest.mark.parametrize("sign", [0, 1])
 def test_grad_matches_oracle(n, dtype, sign):
-    inst, ref_cost = _sat_inst("gr", n, 3, 2 * n)
+    inst, ref_cost = _sat_inst("gr", n, 5, 8 * n)  # the configured gradient workload family (k = 5, r = 8)
     p = 4
     g, b = gen.linear_ramp(p)
     cost, _, _ = api.cost_table(inst)
