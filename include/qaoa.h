@@ -135,6 +135,27 @@ int qaoa_evolve_batch(int batch, int n, const uint8_t *d_costs, int m_max, int p
 int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_state, int dtype, double *p_succ,
                       double *norm, void *stream);
 
+/* Same result as qaoa_success_prob, for callers that cannot allocate device
+ * memory at the point of the call: code capturing into a CUDA graph with a fixed
+ * memory plan, hosts whose own allocator has reserved the device, or paths that
+ * must not risk the implicit synchronisation of cudaMalloc.  The paper has no
+ * counterpart; this is an interface variant of the reduction above.
+ *   Scratch: a fixed device array inside the library (2 x 4096 + 2 doubles,
+ *   about 64 KiB), held by every GPU that loads the library until exit.  The
+ *   call uses at most 4096 blocks, each striding over the state, so every n in
+ *   [1, 32] fits; other n return QAOA_ERANGE.  No cudaMalloc, cudaFree or other
+ *   allocating routine is called; the result is copied into a local host buffer.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: all calls share the array, which keeps the last call's contents;
+ *   every entry a call reads is written earlier in the same call, so nothing
+ *   needs clearing.  Calls whose work overlaps on the GPU (other streams or
+ *   threads) race on the array: serialise them.
+ * Synchronises the stream. */
+int qaoa_success_prob_noalloc(int n, const uint8_t *d_cost, const void *d_state, int dtype, double *p_succ,
+                              double *norm, void *stream);
+
 /* ---- gradient ----------------------------------------------------------------
  * dp_succ/dgamma_l and dp_succ/dbeta_l by a reverse sweep that recomputes the
  * states backward with inverse layers (no stored intermediate states).  The

@@ -705,3 +705,72 @@ extern "C" int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_sta
     *norm = h[1];
     return QAOA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of qaoa_success_prob.  Some callers cannot allocate
+// device memory at the moment they need a result: code running while a CUDA
+// graph is being captured into a fixed memory plan, hosts that pre-reserve the
+// whole device for their own allocator, or signal-safe / real-time paths where
+// a cudaMalloc (which may synchronise the device) is not allowed.  For them the
+// per-block partial sums and the final pair live in this fixed device array,
+// part of the library's image: every GPU that loads the library holds it
+// (2 x 4096 + 2 doubles, about 64 KiB) until the process exits.
+constexpr int NOALLOC_MAX_BLOCKS = 4096;
+static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_BLOCKS + 2];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_addr[256];  // device address of the array, per device ordinal
+
+// Host code cannot use g_noalloc_scratch's name as a device address; the
+// address is looked up once per device with that device current.
+static int noalloc_scratch(double **out) {
+    int dev = 0;
+    QAOA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return set_error(QAOA_ERANGE, "device ordinal %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_success_prob_noalloc(int n, const uint8_t *d_cost, const void *d_state, int dtype,
+                                         double *p_succ, double *norm, void *stream_) {
+    if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", dtype);
+    if (n < 1 || n > QAOA_MAX_N)
+        return set_error(QAOA_ERANGE, "n=%d outside [1, %d] (the fixed scratch serves states of up to 2^%d amplitudes)",
+                         n, QAOA_MAX_N, QAOA_MAX_N);
+    if (!d_cost || !d_state || !p_succ || !norm) return set_error(QAOA_EINVAL, "NULL argument");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int dev = 0, sms = 0;
+    QAOA_CUDA_TRY(cudaGetDevice(&dev));
+    QAOA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    double *scr = nullptr;
+    int rc = noalloc_scratch(&scr);
+    if (rc) return rc;
+    // Each block strides over the state and writes one partial pair, so the
+    // grid (never above NOALLOC_MAX_BLOCKS) bounds the scratch it uses.
+    const uint64_t chunks = ((1ull << n) + (uint64_t)PT * 32 - 1) / ((uint64_t)PT * 32);
+    uint64_t g = (uint64_t)sms * 8;
+    if (g > (uint64_t)NOALLOC_MAX_BLOCKS) g = NOALLOC_MAX_BLOCKS;
+    const int grid = (int)(chunks < g ? chunks : g);
+    double *d_part = scr;                             // [grid][2], all written before they are read
+    double *d_res = scr + 2 * NOALLOC_MAX_BLOCKS;     // [2]
+    if (dtype == QAOA_C64)
+        psucc_kernel<float><<<grid, PT, 0, stream>>>(reinterpret_cast<const float2 *>(d_state), d_cost, n, d_part);
+    else
+        psucc_kernel<double><<<grid, PT, 0, stream>>>(reinterpret_cast<const double2 *>(d_state), d_cost, n, d_part);
+    QAOA_CUDA_TRY(cudaGetLastError());
+    reduce_partials_kernel<<<1, PT, 0, stream>>>(d_part, grid, 2, d_res);
+    QAOA_CUDA_TRY(cudaGetLastError());
+    double h[2];  // pageable host copy: the runtime stages it, nothing is allocated here
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h, d_res, sizeof h, cudaMemcpyDeviceToHost, stream));
+    QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
+    *p_succ = h[0];
+    *norm = h[1];
+    return QAOA_OK;
+}
