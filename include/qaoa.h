@@ -233,11 +233,12 @@ int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits);
 /* The launch sequence of a depth-p evolution: for launch i, the pass of
  * qaoa_plan it runs, its layer l and its mode (0: first pass of layer 0, which
  * generates |+> from the phase table; 1: butterflies of layer l; 2: butterflies
- * of layer l, then the phase and butterflies of layer l + 1 on the same tile).
- * The qubit groups commute within a layer, so their order alternates between
- * layers and each layer boundary costs one pass instead of two.  Returns the
- * number of launches (p * (passes - 1) + 1 for p >= 1) or an error; at most
- * max_launches entries are written. */
+ * of layer l, then the phase and butterflies of layer l + 1 on the same tile;
+ * 3: the phase of layer l at load, then its butterflies).  The qubit groups
+ * commute within a layer, so their order alternates between layers and a
+ * layer boundary on a strided group costs one pass instead of two.  Returns
+ * the number of launches (p * (passes - 1) + 1 when every boundary fuses) or
+ * an error; at most max_launches entries are written. */
 int qaoa_pass_schedule(int n, int p, int dtype, int max_launches, int *pass_index, int *layer, int *mode);
 
 /* Per-kernel timing: when enabled, every kernel the library launches is

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 if (LOW) {  // all of M_l undone: phase term, then D_l^dagger
-                    const int cst = pc[r * ss];
+                    const int cst = __ldg(pc + r * ss);  // read-only path: no aliasing with the stores
                     gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
                     const V ph = stab[cst];
                     vp[r] = cmul(vp[r], ph);

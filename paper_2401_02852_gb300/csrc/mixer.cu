@@ -41,12 +41,13 @@ struct PhaseTab {
     typename Cx<R>::V t[NT];
 };
 
-// Pass modes.  INIT: the first pass of layer 0 (the state is |+>, the table
-// holds the amplitude times the phase).  PLAIN: butterflies of one layer.
-// FUSED: butterflies of layer l on the pass's qubits, the phase of layer l+1,
-// then the butterflies of layer l+1 on the same qubits (the pass is the last
-// of layer l and the first of layer l+1; the qubit factors commute, so the
-// group order alternates between layers).
+// Pass modes (MODE_* in the internal header): INIT generates layer 0's state
+// from the phase table, PHASE multiplies by a layer's phase at load, PLAIN only
+// butterflies, FUSED butterflies layer l, applies the phase of layer l + 1 in
+// the tile and butterflies layer l + 1 (the pass is the last of layer l and the
+// first of layer l + 1; the qubit factors commute, so the group order
+// alternates between layers).
+
 // The rounds of one layer from the load mapping (8) to the store mapping (LC)...
 template <typename G, bool LOW, bool UA>
 __device__ __forceinline__ void rounds_up(typename G::V *v, typename G::V *tile, uint32_t active, typename G::Real A,
@@ -81,7 +82,8 @@ __device__ __forceinline__ void rounds_down(typename G::V *v, typename G::V *til
 
 // Stores the tile (thread pointer + r * stride), fusing the p_succ / norm
 // partials and the adjoint seed P psi when this is the evolution's last pass.
-template <typename R>
+// sc: the tile's cost bytes in shared memory, indexed by tile element.
+template <typename R, int LO>
 __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename Cx<R>::V *sp, const uint8_t *sc,
                                            typename Cx<R>::V *sa, uint64_t stride, bool reduce, double acc[2]) {
     using V = typename Cx<R>::V;
@@ -89,14 +91,16 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
     // Opaque to the compiler: otherwise it keeps the load phase's 32 offsets
     // r * stride live across the whole tile to reuse them here.
     asm volatile("" : "+l"(sp), "+l"(stride));
-    R ps = 0, nm = 0;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        sp[r * stride] = v[r];
-        if (reduce) {
+    for (int r = 0; r < NR; ++r) sp[r * stride] = v[r];
+    if (reduce) {
+        R ps = 0, nm = 0;
+        const uint32_t tid = threadIdx.x;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
             const R w = v[r].x * v[r].x + v[r].y * v[r].y;
             nm += w;
-            const bool sol = sc[r * stride] == 0;
+            const bool sol = sc[tile_elem<Cx<R>, LO>(tid, r)] == 0;
             if (sol) ps += w;
             if (sa) {
                 V z;
@@ -105,23 +109,25 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
                 sa[r * stride] = z;
             }
         }
+        acc[0] += (double)ps;
+        acc[1] += (double)nm;
     }
-    acc[0] += (double)ps;
-    acc[1] += (double)nm;
 }
 
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
-                                           typename Cx<R>::V *tile) {
+                                           typename Cx<R>::V *tile, uint8_t *sc) {
     using G = Cx<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
     constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
+    constexpr int CH = (1 << T) / 16 / PT;  // 16-byte chunks of cost bytes per thread
     const uint32_t tid = threadIdx.x;
     const size_t inst = blockIdx.y;
     V *st = a.state + (inst << a.n);
     V *adj = a.adj ? a.adj + (inst << a.n) : nullptr;
     const uint8_t *cs = a.cost + (inst << a.n);
+    const bool need_c = MODE != MODE_PLAIN || a.reduce;
     // Every tile address is thread pointer + r * stride (the plan keeps the row
     // width at 4 bits in high passes, so the register bits are all strided).
     const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<G, 8>(tid, 0), a.row, a.lo);
@@ -131,28 +137,41 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     for (uint64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
         const uint64_t base = tile_base(t, a.row, a.lo, T);
-        V v[NR];
-        {  // load (mapping 8: coalesced); layer 0 starts from the table
-            const V *lp = st + base + ld_t;
-            const uint8_t *lc = cs + base + ld_t;
+        // The tile's cost bytes: 16-byte chunks (a row of a high tile, or 16
+        // consecutive bytes of a low tile) through the read-only path, issued
+        // first so their latency overlaps the state loads.
+        uint4 cc[CH];
+        if (need_c) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) v[r] = MODE == MODE_INIT ? stab[lc[r * ld_s]] : lp[r * ld_s];
+            for (int j = 0; j < CH; ++j)
+                cc[j] = __ldg(reinterpret_cast<const uint4 *>(cs + base +
+                                                              elem_offset(16u * (tid + j * PT), a.row, a.lo)));
+            __syncthreads();  // the previous tile's readers of sc are done
+#pragma unroll
+            for (int j = 0; j < CH; ++j) reinterpret_cast<uint4 *>(sc)[tid + j * PT] = cc[j];
         }
-        rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1);
-        if (MODE == MODE_FUSED) {
-            {  // phase of layer l+1 in the LC mapping
-                const uint8_t *pc = cs + base + st_t;
-                uint64_t ps = st_s;
-                asm volatile("" : "+l"(pc), "+l"(ps));  // not hoisted above the rounds of layer l
+        V v[NR];
+        if (MODE == MODE_INIT || MODE == MODE_PHASE) {
+            __syncthreads();  // sc complete
+            const V *lp = st + base + ld_t;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[pc[r * ps]]);
+            for (int r = 0; r < NR; ++r) {
+                const V ph = stab[sc[tile_elem<G, 8>(tid, r)]];
+                v[r] = MODE == MODE_INIT ? ph : cmul(lp[r * ld_s], ph);
             }
+        } else {  // load (mapping 8: coalesced)
+            const V *lp = st + base + ld_t;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = lp[r * ld_s];
+        }
+        rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1);  // its first exchange publishes sc
+        if (MODE == MODE_FUSED) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
             rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2);
-            store_tile<R>(v, st + base + ld_t, cs + base + ld_t, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce,
-                          acc);
+            store_tile<R, 8>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce, acc);
         } else {
-            store_tile<R>(v, st + base + st_t, cs + base + st_t, adj ? adj + base + st_t : nullptr, st_s, a.reduce,
-                          acc);
+            store_tile<R, LC>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce, acc);
         }
     }
     if (a.reduce) {
@@ -165,6 +184,13 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     }
 }
 
+// Shared-memory phase table length: at least 256 entries (any uint8 cost
+// indexes inside it), a multiple of 16 so the cost tile after it stays aligned.
+__host__ __device__ __forceinline__ int table_entries(int m) {
+    const int e = m < 255 ? 256 : m + 1;
+    return (e + 15) & ~15;
+}
+
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT>
@@ -174,6 +200,7 @@ __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ Pas
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
     V *stab = tile + (1 << Cx<R>::T);
+    uint8_t *sc = reinterpret_cast<uint8_t *>(stab + (MODE == MODE_PLAIN ? 0 : table_entries(a.m)));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
             V z;
@@ -182,7 +209,7 @@ __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ Pas
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, tile);
+    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, tile, sc);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -362,9 +389,12 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 // ---------------------------------------------------------------------------
 // Host side of the multi-pass evolution.
 
+// Dynamic shared memory of a pass: the tile, the phase table (modes that apply
+// a phase) and the tile's cost bytes.
 template <typename R>
 static size_t pass_smem(bool phase, int m) {
-    return sizeof(typename Cx<R>::V) * ((size_t(1) << Cx<R>::T) + (phase ? (size_t)(m < 255 ? 256 : m + 1) : 0));
+    const size_t T = size_t(1) << Cx<R>::T;
+    return sizeof(typename Cx<R>::V) * (T + (phase ? (size_t)table_entries(m) : 0)) + T;
 }
 
 template <typename R>
@@ -373,30 +403,32 @@ struct PassKernels {
     using None = PhaseTab<R, 1>;
     using KFull = void (*)(PassArgs<R>, Full);
     using KNone = void (*)(PassArgs<R>, None);
-    // [ua1] for init / plain, [low][ua1][ua2] for fused
-    KFull init_k[2] = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE>,
-                       pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE>};
-    KNone plain_low[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1>,
-                          pass_kernel<R, true, MODE_PLAIN, true, false, 1>};
-    KNone plain_high[2] = {pass_kernel<R, false, MODE_PLAIN, false, false, 1>,
-                           pass_kernel<R, false, MODE_PLAIN, true, false, 1>};
-    KFull fused[2][2][2] = {{{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE>,
-                              pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE>},
-                             {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE>,
-                              pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE>}},
-                            {{pass_kernel<R, true, MODE_FUSED, false, false, MAX_TABLE>,
-                              pass_kernel<R, true, MODE_FUSED, false, true, MAX_TABLE>},
-                             {pass_kernel<R, true, MODE_FUSED, true, false, MAX_TABLE>,
-                              pass_kernel<R, true, MODE_FUSED, true, true, MAX_TABLE>}}};
+    // [low][ua1] for init / plain, [ua1] for phase-at-load (low) and
+    // [ua1][ua2] for fused (high: the low pass never fuses)
+    KFull init_k[2][2] = {{pass_kernel<R, false, MODE_INIT, false, false, MAX_TABLE>,
+                           pass_kernel<R, false, MODE_INIT, true, false, MAX_TABLE>},
+                          {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE>,
+                           pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE>}};
+    KFull phase_low[2] = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE>,
+                          pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE>};
+    KNone plain[2][2] = {{pass_kernel<R, false, MODE_PLAIN, false, false, 1>,
+                          pass_kernel<R, false, MODE_PLAIN, true, false, 1>},
+                         {pass_kernel<R, true, MODE_PLAIN, false, false, 1>,
+                          pass_kernel<R, true, MODE_PLAIN, true, false, 1>}};
+    KFull fused[2][2] = {{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE>,
+                          pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE>},
+                         {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE>,
+                          pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE>}};
     cudaError_t init() {
         const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
         std::vector<const void *> ks;
         for (int i = 0; i < 2; ++i) {
-            ks.push_back((const void *)init_k[i]);
-            ks.push_back((const void *)plain_low[i]);
-            ks.push_back((const void *)plain_high[i]);
-            for (int j = 0; j < 2; ++j)
-                for (int k = 0; k < 2; ++k) ks.push_back((const void *)fused[i][j][k]);
+            ks.push_back((const void *)phase_low[i]);
+            for (int j = 0; j < 2; ++j) {
+                ks.push_back((const void *)init_k[i][j]);
+                ks.push_back((const void *)plain[i][j]);
+                ks.push_back((const void *)fused[i][j]);
+            }
         }
         for (const void *k : ks) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -508,14 +540,17 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         const int u1 = a.ua1 ? 1 : 0, u2 = a.ua2 ? 1 : 0;
         if (L.mode == MODE_INIT) {
             fill_table<R>(tab, r, 0, sign);
-            pk->init_k[u1]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            pk->init_k[low][u1]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+        } else if (L.mode == MODE_PHASE) {
+            if (!low) return set_error(QAOA_ECUDA, "schedule: phase-at-load on a strided pass");
+            fill_table<R>(tab, r, L.la, sign);
+            pk->phase_low[u1]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
         } else if (L.mode == MODE_FUSED) {
+            if (low) return set_error(QAOA_ECUDA, "schedule: fused low pass");
             fill_table<R>(tab, r, L.la + 1, sign);
-            pk->fused[low ? 1 : 0][u1][u2]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
-        } else if (low) {
-            pk->plain_low[u1]<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            pk->fused[u1][u2]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
         } else {
-            pk->plain_high[u1]<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            pk->plain[low][u1]<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
         }
         rc = profile_after(kind, stream);
         if (rc) return rc;

@@ -90,14 +90,18 @@ int make_plan(int n, int dtype, Plan *plan);
 int make_plan_geo(int n, int T, int gmax, Plan *plan);
 
 // One launch of the forward evolution: pass `pass` of the plan for layer `la`.
-// Modes: 0 = first pass of layer 0 (state |+> generated from the phase table),
-// 1 = butterflies of one layer, 2 = butterflies of layer la, the phase of
-// layer la + 1 and the butterflies of layer la + 1 (the group order alternates
-// between layers so the last pass of a layer and the first of the next fuse).
+// Modes: 0 = first pass of layer 0 (the state |+> is generated from the phase
+// table), 1 = butterflies of one layer, 2 = butterflies of layer la, the phase
+// of layer la + 1 and the butterflies of layer la + 1 on the same tile,
+// 3 = the phase of layer la applied at load, then its butterflies.
+// The qubit groups of a layer commute, so their order alternates between
+// layers and the last pass of a layer fuses with the first of the next; the
+// low pass always sits inside a layer (its fused form would be bound by the
+// SMs rather than by HBM), so only high passes fuse.
 struct Launch {
     int pass, la, mode;
 };
-enum PassMode { MODE_INIT = 0, MODE_PLAIN = 1, MODE_FUSED = 2 };
+enum PassMode { MODE_INIT = 0, MODE_PLAIN = 1, MODE_FUSED = 2, MODE_PHASE = 3 };
 std::vector<Launch> make_schedule(int n_passes, int p);
 
 // ---------------------------------------------------------------------------

@@ -184,13 +184,32 @@ std::vector<Launch> make_schedule(int n_passes, int p) {
         out.push_back({0, 0, MODE_INIT});
         return out;
     }
+    // Pass orders of even and odd layers.  With two or more high groups the low
+    // pass (index 0) is second, so both ends of every layer are high groups and
+    // each layer boundary fuses.  With one high group the orders are [0, 1] and
+    // [1, 0]: the boundary on group 1 fuses, the one on the low pass does not.
+    const int k = n_passes - 1;
+    std::vector<int> even, odd;
+    if (k >= 2) {
+        even.push_back(1);
+        even.push_back(0);
+        for (int g = 2; g <= k; ++g) even.push_back(g);
+        odd.push_back(k);
+        odd.push_back(0);
+        for (int g = k - 1; g >= 1; --g) odd.push_back(g);
+    } else {
+        even = {0, 1};
+        odd = {1, 0};
+    }
     for (int l = 0; l < p; ++l) {
+        const std::vector<int> &ord = (l % 2 == 0) ? even : odd;
         for (int j = 0; j < n_passes; ++j) {
-            if (l > 0 && j == 0) continue;  // fused into the previous layer's last pass
-            const int ps = (l % 2 == 0) ? j : n_passes - 1 - j;
+            const int ps = ord[j];
+            const bool first = j == 0, last = j == n_passes - 1;
+            if (l > 0 && first && ps != 0) continue;  // fused into the previous layer's last pass
             int mode = MODE_PLAIN;
-            if (l == 0 && j == 0) mode = MODE_INIT;
-            if (j == n_passes - 1 && l + 1 < p) mode = MODE_FUSED;
+            if (first) mode = (l == 0) ? MODE_INIT : MODE_PHASE;
+            if (last && l + 1 < p && ps != 0) mode = MODE_FUSED;
             out.push_back({ps, l, mode});
         }
     }

@@ -122,18 +122,23 @@ def test_schedule_applies_each_layer_in_order(lib, dtype, T, p):
             return list(range(lo + G - bits, lo + G))
 
         events = []
-        for pi, l, mode in _schedule(lib, n, p, dtype):
-            if mode == 0:
-                events.append(("phase", 0, None))
+        sched = _schedule(lib, n, p, dtype)
+        for pi, l, mode in sched:
+            if mode in (0, 3):
+                events.append(("phase", l, None))
             if p > 0:
                 events += [("mix", l, q) for q in qubits(pi)]
             if mode == 2:
+                assert pi != 0  # the low pass never fuses
                 events.append(("phase", l + 1, None))
                 events += [("mix", l + 1, q) for q in qubits(pi)]
         if p == 0:
             assert events == [("phase", 0, None)]
             continue
-        assert len(_schedule(lib, n, p, dtype)) == p * (len(passes) - 1) + 1
+        if len(passes) >= 3:  # every layer boundary fuses
+            assert len(sched) == p * (len(passes) - 1) + 1
+        else:  # one high group: the boundaries on it fuse, those on the low pass do not
+            assert len(sched) == 2 * p - p // 2
         layer, seen = -1, None
         for kind, l, q in events:
             if kind == "phase":
