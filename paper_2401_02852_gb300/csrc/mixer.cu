@@ -114,57 +114,99 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
     }
 }
 
+// cp.async (LDGSTS) helpers: 16-byte global -> shared copies that complete in
+// the background; completion is a hardware wait on the thread's commit groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Issues the copies of tile `base` into (buf, sc): the state as 16-byte chunks
+// (the tile's rows of 2^row amplitudes are whole numbers of chunks) and, when
+// needed, its cost bytes (one 16-byte chunk per row of 16 amplitudes).  Chunk q
+// of the tile lands at byte 16 q of the buffer, i.e. tile element u sits at
+// buf[u]; thread tid takes chunks tid + PT j, whose addresses are a thread
+// base plus j times a stride.
+template <typename R, bool LOW>
+__device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const uint8_t *cs, uint64_t base, int row,
+                                           int lo, bool state, bool cost, typename Cx<R>::V *buf, uint8_t *sc) {
+    using V = typename Cx<R>::V;
+    constexpr int T = Cx<R>::T;
+    constexpr int EPC = 16 / (int)sizeof(V);            // amplitudes per 16-byte chunk
+    constexpr int NCH = (1 << T) / EPC / PT;             // state chunks per thread
+    constexpr int CCH = (1 << T) / 16 / PT;              // cost chunks per thread
+    const uint32_t tid = threadIdx.x;
+    if (state) {
+        // chunk q = tid + PT j covers tile elements [EPC q, EPC q + EPC)
+        const uint64_t u0 = (uint64_t)EPC * tid;
+        const uint64_t off0 = elem_offset((uint32_t)u0, row, lo);
+        const uint64_t step = elem_offset((uint32_t)(EPC * PT), row, lo);  // tile bits of EPC*PT are all strided or all contiguous
+        const V *src = st + base + off0;
+        char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * PT * j, src + step * j);
+    }
+    if (cost) {
+        const uint64_t off0 = elem_offset(16u * tid, row, lo);
+        const uint64_t step = elem_offset(16u * PT, row, lo);
+        const uint8_t *src = cs + base + off0;
+#pragma unroll
+        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + PT * j), src + step * j);
+    }
+}
+
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
-                                           typename Cx<R>::V *tile, uint8_t *sc) {
+                                           typename Cx<R>::V *bufs, uint8_t *scs) {
     using G = Cx<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
     constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
-    constexpr int CH = (1 << T) / 16 / PT;  // 16-byte chunks of cost bytes per thread
     const uint32_t tid = threadIdx.x;
     const size_t inst = blockIdx.y;
     V *st = a.state + (inst << a.n);
     V *adj = a.adj ? a.adj + (inst << a.n) : nullptr;
     const uint8_t *cs = a.cost + (inst << a.n);
     const bool need_c = MODE != MODE_PLAIN || a.reduce;
-    // Every tile address is thread pointer + r * stride (the plan keeps the row
-    // width at 4 bits in high passes, so the register bits are all strided).
+    const bool need_s = MODE != MODE_INIT;
+    // Stores go straight from registers: thread pointer + r * stride (the plan
+    // keeps the row width at 4 bits in high passes, so register bits are strided).
     const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<G, 8>(tid, 0), a.row, a.lo);
     const uint64_t ld_s = LOW ? 256u : (1ull << (a.lo + 8 - a.row));
     const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
     const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
     double acc[2] = {0.0, 0.0};  // p_succ, norm
-    for (uint64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+    uint64_t t = blockIdx.x;
+    if (t < a.tiles)
+        issue_tile<R, LOW>(st, cs, tile_base(t, a.row, a.lo, T), a.row, a.lo, need_s, need_c, bufs, scs);
+    cp_async_commit();
+    for (int i = 0; t < a.tiles; ++i, t += gridDim.x) {
+        const int b = i & 1;
+        V *tile = bufs + ((size_t)b << T);
+        uint8_t *sc = scs + ((size_t)b << T);
         const uint64_t base = tile_base(t, a.row, a.lo, T);
-        // The tile's cost bytes: 16-byte chunks (a row of a high tile, or 16
-        // consecutive bytes of a low tile) through the read-only path, issued
-        // first so their latency overlaps the state loads.
-        uint4 cc[CH];
-        if (need_c) {
-#pragma unroll
-            for (int j = 0; j < CH; ++j)
-                cc[j] = __ldg(reinterpret_cast<const uint4 *>(cs + base +
-                                                              elem_offset(16u * (tid + j * PT), a.row, a.lo)));
-            __syncthreads();  // the previous tile's readers of sc are done
-#pragma unroll
-            for (int j = 0; j < CH; ++j) reinterpret_cast<uint4 *>(sc)[tid + j * PT] = cc[j];
-        }
+        // prefetch the next tile into the other buffer while this one computes
+        const uint64_t tn = t + gridDim.x;
+        if (tn < a.tiles)
+            issue_tile<R, LOW>(st, cs, tile_base(tn, a.row, a.lo, T), a.row, a.lo, need_s, need_c,
+                               bufs + ((size_t)(b ^ 1) << T), scs + ((size_t)(b ^ 1) << T));
+        cp_async_commit();
+        cp_async_wait_prev();  // this tile's copies (all but the newest group) are done
+        __syncthreads();
         V v[NR];
-        if (MODE == MODE_INIT || MODE == MODE_PHASE) {
-            __syncthreads();  // sc complete
-            const V *lp = st + base + ld_t;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const V ph = stab[sc[tile_elem<G, 8>(tid, r)]];
-                v[r] = MODE == MODE_INIT ? ph : cmul(lp[r * ld_s], ph);
-            }
-        } else {  // load (mapping 8: coalesced)
-            const V *lp = st + base + ld_t;
-#pragma unroll
-            for (int r = 0; r < NR; ++r) v[r] = lp[r * ld_s];
+        for (int r = 0; r < NR; ++r) {  // mapping 8 on the dense buffer: consecutive lanes, no conflicts
+            const uint32_t u = tile_elem<G, 8>(tid, r);
+            if (MODE == MODE_INIT)
+                v[r] = stab[sc[u]];
+            else if (MODE == MODE_PHASE)
+                v[r] = cmul(tile[u], stab[sc[u]]);
+            else
+                v[r] = tile[u];
         }
-        rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1);  // its first exchange publishes sc
+        rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1);
         if (MODE == MODE_FUSED) {
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
@@ -173,6 +215,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         } else {
             store_tile<R, LC>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce, acc);
         }
+        __syncthreads();  // every thread is done with this buffer before it is refilled
     }
     if (a.reduce) {
         block_sum<2>(acc);
@@ -185,22 +228,25 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
 }
 
 // Shared-memory phase table length: at least 256 entries (any uint8 cost
-// indexes inside it), a multiple of 16 so the cost tile after it stays aligned.
+// indexes inside it), a multiple of 16 so what follows stays aligned.
 __host__ __device__ __forceinline__ int table_entries(int m) {
     const int e = m < 255 ? 256 : m + 1;
     return (e + 15) & ~15;
 }
 
+// One CTA per SM, persistent over tiles, double-buffered: two state buffers,
+// two cost-byte buffers, then the phase table.
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT>
-__global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
+__global__ void __launch_bounds__(PT, 1) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                      const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
+    constexpr int T = Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *tile = reinterpret_cast<V *>(smem_raw);
-    V *stab = tile + (1 << Cx<R>::T);
-    uint8_t *sc = reinterpret_cast<uint8_t *>(stab + (MODE == MODE_PLAIN ? 0 : table_entries(a.m)));
+    V *bufs = reinterpret_cast<V *>(smem_raw);
+    uint8_t *scs = reinterpret_cast<uint8_t *>(bufs + (2 << T));
+    V *stab = reinterpret_cast<V *>(scs + (2 << T));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
             V z;
@@ -209,7 +255,7 @@ __global__ void __launch_bounds__(PT, 2) pass_kernel(const __grid_constant__ Pas
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, tile, sc);
+    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, bufs, scs);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -389,12 +435,12 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 // ---------------------------------------------------------------------------
 // Host side of the multi-pass evolution.
 
-// Dynamic shared memory of a pass: the tile, the phase table (modes that apply
-// a phase) and the tile's cost bytes.
+// Dynamic shared memory of a pass: two tile buffers, two cost-byte buffers and
+// the phase table (modes that apply a phase).
 template <typename R>
 static size_t pass_smem(bool phase, int m) {
     const size_t T = size_t(1) << Cx<R>::T;
-    return sizeof(typename Cx<R>::V) * (T + (phase ? (size_t)table_entries(m) : 0)) + T;
+    return 2 * sizeof(typename Cx<R>::V) * T + 2 * T + (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
 template <typename R>
@@ -466,7 +512,7 @@ int pass_grid_x(int dtype, int n, int batch) {
     DeviceInfo di;
     if (device_info(&di)) return -1;
     const int T = dtype == QAOA_C64 ? Cx<float>::T : Cx<double>::T;
-    return grid_x(di.sms, 2, batch, 1ull << (n - T));
+    return grid_x(di.sms, 1, batch, 1ull << (n - T));  // one persistent CTA per SM
 }
 
 template <typename R>
