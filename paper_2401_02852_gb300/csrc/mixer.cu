@@ -48,36 +48,46 @@ struct PhaseTab {
 // first of layer l + 1; the qubit factors commute, so the group order
 // alternates between layers).
 
-// The rounds of one layer from the load mapping (8) to the store mapping (LC)...
+// Mapping of the last round of a pass (its stores are coalesced too).
+template <typename G, bool LOW>
+struct LastLO {
+    static constexpr int value = PassRounds<G, LOW>::LAST;
+};
+
+// The rounds of one layer from the load mapping to the last mapping...
 template <typename G, bool LOW, bool UA>
 __device__ __forceinline__ void rounds_up(typename G::V *v, typename G::V *tile, uint32_t active, typename G::Real A,
                                           typename G::Real B) {
-    constexpr int T = G::T, LC = LOW ? G::LC_LOW : G::LC_HIGH;
-    reg_butterflies<G, UA, 8, T>(v, active, A, B);
-    if (LOW) {
-        exchange<G, 8, 0>(v, tile);
-        reg_butterflies<G, UA, 0, T>(v, active, A, B);
-        exchange<G, 0, LC>(v, tile);
-    } else {
-        exchange<G, 8, LC>(v, tile);
+    using P = PassRounds<G, LOW>;
+    mask_butterflies<G, UA, P::R0::LO, P::R0::MASK>(v, active, A, B);
+    exchange<G, P::R0::LO, P::R1::LO>(v, tile);
+    mask_butterflies<G, UA, P::R1::LO, P::R1::MASK>(v, active, A, B);
+    if constexpr (P::N > 2) {
+        exchange<G, P::R1::LO, P::R2::LO>(v, tile);
+        mask_butterflies<G, UA, P::R2::LO, P::R2::MASK>(v, active, A, B);
     }
-    reg_butterflies<G, UA, LC, 8>(v, active, A, B);
+    if constexpr (P::N > 3) {
+        exchange<G, P::R2::LO, P::R3::LO>(v, tile);
+        mask_butterflies<G, UA, P::R3::LO, P::R3::MASK>(v, active, A, B);
+    }
 }
 
-// ... and back from LC to 8 (same qubits, reverse round order).
+// ... and back from the last mapping to the load mapping (same qubits).
 template <typename G, bool LOW, bool UA>
 __device__ __forceinline__ void rounds_down(typename G::V *v, typename G::V *tile, uint32_t active,
                                             typename G::Real A, typename G::Real B) {
-    constexpr int T = G::T, LC = LOW ? G::LC_LOW : G::LC_HIGH;
-    reg_butterflies<G, UA, LC, 8>(v, active, A, B);
-    if (LOW) {
-        exchange<G, LC, 0>(v, tile);
-        reg_butterflies<G, UA, 0, T>(v, active, A, B);
-        exchange<G, 0, 8>(v, tile);
-    } else {
-        exchange<G, LC, 8>(v, tile);
+    using P = PassRounds<G, LOW>;
+    if constexpr (P::N > 3) {
+        mask_butterflies<G, UA, P::R3::LO, P::R3::MASK>(v, active, A, B);
+        exchange<G, P::R3::LO, P::R2::LO>(v, tile);
     }
-    reg_butterflies<G, UA, 8, T>(v, active, A, B);
+    if constexpr (P::N > 2) {
+        mask_butterflies<G, UA, P::R2::LO, P::R2::MASK>(v, active, A, B);
+        exchange<G, P::R2::LO, P::R1::LO>(v, tile);
+    }
+    mask_butterflies<G, UA, P::R1::LO, P::R1::MASK>(v, active, A, B);
+    exchange<G, P::R1::LO, P::R0::LO>(v, tile);
+    mask_butterflies<G, UA, P::R0::LO, P::R0::MASK>(v, active, A, B);
 }
 
 // Stores the tile (thread pointer + r * stride), fusing the p_succ / norm
@@ -135,25 +145,28 @@ __device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const ui
     using V = typename Cx<R>::V;
     constexpr int T = Cx<R>::T;
     constexpr int EPC = 16 / (int)sizeof(V);            // amplitudes per 16-byte chunk
-    constexpr int NCH = (1 << T) / EPC / PT;             // state chunks per thread
-    constexpr int CCH = (1 << T) / 16 / PT;              // cost chunks per thread
+    constexpr int NT = Cx<R>::PT;
+    constexpr int NCH = (1 << T) / EPC / NT;             // state chunks per thread
+    constexpr int CCH = (1 << T) / 16 / NT;              // cost chunks per thread
     const uint32_t tid = threadIdx.x;
     if (state) {
         // chunk q = tid + PT j covers tile elements [EPC q, EPC q + EPC)
         const uint64_t u0 = (uint64_t)EPC * tid;
         const uint64_t off0 = elem_offset((uint32_t)u0, row, lo);
-        const uint64_t step = elem_offset((uint32_t)(EPC * PT), row, lo);  // tile bits of EPC*PT are all strided or all contiguous
+        // the bits of EPC * NT * j lie above those of EPC * tid and above the row
+        // bits, so the offset is linear in j
+        const uint64_t step = elem_offset((uint32_t)(EPC * NT), row, lo);
         const V *src = st + base + off0;
         char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
 #pragma unroll
-        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * PT * j, src + step * j);
+        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * NT * j, src + step * j);
     }
     if (cost) {
         const uint64_t off0 = elem_offset(16u * tid, row, lo);
-        const uint64_t step = elem_offset(16u * PT, row, lo);
+        const uint64_t step = elem_offset(16u * NT, row, lo);
         const uint8_t *src = cs + base + off0;
 #pragma unroll
-        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + PT * j), src + step * j);
+        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + NT * j), src + step * j);
     }
 }
 
@@ -163,7 +176,8 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     using G = Cx<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
-    constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
+    constexpr int LD = G::LOAD;                // first round's mapping
+    constexpr int LC = LastLO<G, LOW>::value;  // last round's mapping
     const uint32_t tid = threadIdx.x;
     const size_t inst = blockIdx.y;
     V *st = a.state + (inst << a.n);
@@ -172,9 +186,10 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     const bool need_c = MODE != MODE_PLAIN || a.reduce;
     const bool need_s = MODE != MODE_INIT;
     // Stores go straight from registers: thread pointer + r * stride (the plan
-    // keeps the row width at 4 bits in high passes, so register bits are strided).
-    const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<G, 8>(tid, 0), a.row, a.lo);
-    const uint64_t ld_s = LOW ? 256u : (1ull << (a.lo + 8 - a.row));
+    // keeps the row width at 4 bits in high passes and both store mappings put
+    // the registers above bit 4, so register bits are strided).
+    const uint64_t ld_t = elem_offset(tile_elem<G, LD>(tid, 0), a.row, a.lo);
+    const uint64_t ld_s = LOW ? (1ull << LD) : (1ull << (a.lo + LD - a.row));
     const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
     const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
     double acc[2] = {0.0, 0.0};  // p_succ, norm
@@ -197,8 +212,8 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         __syncthreads();
         V v[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {  // mapping 8 on the dense buffer: consecutive lanes, no conflicts
-            const uint32_t u = tile_elem<G, 8>(tid, r);
+        for (int r = 0; r < NR; ++r) {  // load mapping on the dense buffer: consecutive lanes, no conflicts
+            const uint32_t u = tile_elem<G, LD>(tid, r);
             if (MODE == MODE_INIT)
                 v[r] = stab[sc[u]];
             else if (MODE == MODE_PHASE)
@@ -211,14 +226,14 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
             rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2);
-            store_tile<R, 8>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce, acc);
+            store_tile<R, LD>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce, acc);
         } else {
             store_tile<R, LC>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce, acc);
         }
         __syncthreads();  // every thread is done with this buffer before it is refilled
     }
     if (a.reduce) {
-        block_sum<2>(acc);
+        block_sum<2, G::PT>(acc);
         if (threadIdx.x == 0) {
             double *out = a.partials + 2 * (inst * gridDim.x + blockIdx.x);
             out[0] = acc[0];
@@ -239,8 +254,8 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT>
-__global__ void __launch_bounds__(PT, 1) pass_kernel(const __grid_constant__ PassArgs<R> a,
-                                                     const __grid_constant__ PhaseTab<R, NT> tab) {
+__global__ void __launch_bounds__(Cx<R>::PT, 1) pass_kernel(const __grid_constant__ PassArgs<R> a,
+                                                            const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
     constexpr int T = Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(PT, 1) pass_kernel(const __grid_constant__ Pas
     uint8_t *scs = reinterpret_cast<uint8_t *>(bufs + (2 << T));
     V *stab = reinterpret_cast<V *>(scs + (2 << T));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
-        for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
+        for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) {
             V z;
             z.x = z.y = 0;
             stab[i] = i <= a.m ? tab.t[i] : z;
@@ -545,7 +560,7 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
     auto *tab = reinterpret_cast<typename PassKernels<R>::Full *>(tbuf.data());
     typename PassKernels<R>::None none{};
     const std::vector<Launch> seq = make_schedule(pl.n_passes, r.p);
-    const dim3 block(PT), grid(gx, r.batch);
+    const dim3 block(Cx<R>::PT), grid(gx, r.batch);
     for (size_t i = 0; i < seq.size(); ++i) {
         const Launch &L = seq[i];
         const Pass &ps = pl.pass[L.pass];

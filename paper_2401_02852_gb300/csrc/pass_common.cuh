@@ -26,10 +26,12 @@ namespace qaoa {
 
 constexpr int PT = 256;  // threads per pass CTA (8 thread bits)
 
-// Tile geometry: element type R, 2^T amplitudes per tile, 2^RB per thread.
-// LC_LOW / LC_HIGH are the store mappings of the low and high passes; the
-// swizzle spreads the bits that lanes run along over the shared-memory banks
-// (checked conflict-free for every mapping used).
+// Tile geometry: element type R, 2^T amplitudes per tile, 2^RB per thread,
+// 2^(T - RB) threads.  The load mapping (LO = T - RB) puts the registers on the
+// top RB tile bits, so lanes run along tile bits 0..4 (coalesced, and dense in
+// shared memory).  The swizzle spreads the bits that lanes run along in the
+// other mappings over the shared-memory banks (checked conflict-free for every
+// mapping used).
 template <typename R, int T_, int RB_>
 struct Geo {
     using V = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
@@ -37,20 +39,23 @@ struct Geo {
     static constexpr int T = T_;
     static constexpr int RB = RB_;
     static constexpr int NR = 1 << RB_;
-    static constexpr int LC_LOW = RB_;  // after the rounds at 8 and 0
+    static constexpr int TB = T_ - RB_;
+    static constexpr int PT = 1 << TB;
+    static constexpr int LOAD = TB;
+    static constexpr int LC_LOW = RB_;  // adjoint passes: rounds at 8, 0, RB
     static constexpr int LC_HIGH = 4;
     static constexpr int SW_SHIFT = RB_;
     static constexpr uint32_t SW_MASK = sizeof(R) == 4 ? 15u : 7u;
-    static_assert(T_ - RB_ == 8, "256 threads own the tile");
     __device__ static __forceinline__ uint32_t swz(uint32_t u) { return u ^ ((u >> SW_SHIFT) & SW_MASK); }
 };
 
-// Forward geometry: 64 KiB tiles (2^13 complex64 / 2^12 complex128).
+// Forward geometry: 64 KiB tiles; complex64 with 512 threads x 16 amplitudes,
+// complex128 with 256 threads x 16 amplitudes.
 template <typename R>
 struct FwdGeoT;
 template <>
 struct FwdGeoT<float> {
-    using type = Geo<float, 13, 5>;
+    using type = Geo<float, 13, 4>;
 };
 template <>
 struct FwdGeoT<double> {
@@ -58,6 +63,48 @@ struct FwdGeoT<double> {
 };
 template <typename R>
 using Cx = typename FwdGeoT<R>::type;
+
+// A round: the mapping LO and the tile bits it butterflies (compile time; the
+// pass's runtime mask of active bits is applied on top).
+template <int LO_, uint32_t MASK_>
+struct Round {
+    static constexpr int LO = LO_;
+    static constexpr uint32_t MASK = MASK_;
+};
+
+// The rounds of the low pass (all T tile bits) and of a high pass (tile bits
+// [4, T): rows of 16 contiguous amplitudes), per forward geometry.  The first
+// round is the load mapping; the last round's mapping is also coalesced.
+template <typename G, bool LOW>
+struct PassRounds;
+template <>
+struct PassRounds<Geo<float, 13, 4>, true> {
+    static constexpr int N = 4, LAST = 5;
+    using R0 = Round<9, 0x1E00>;
+    using R1 = Round<0, 0x000F>;
+    using R2 = Round<4, 0x00F0>;
+    using R3 = Round<5, 0x0100>;
+};
+template <>
+struct PassRounds<Geo<float, 13, 4>, false> {
+    static constexpr int N = 3, LAST = 5;
+    using R0 = Round<9, 0x1E00>;
+    using R1 = Round<4, 0x00F0>;
+    using R2 = Round<5, 0x0100>;
+};
+template <>
+struct PassRounds<Geo<double, 12, 4>, true> {
+    static constexpr int N = 3, LAST = 4;
+    using R0 = Round<8, 0xF00>;
+    using R1 = Round<0, 0x00F>;
+    using R2 = Round<4, 0x0F0>;
+};
+template <>
+struct PassRounds<Geo<double, 12, 4>, false> {
+    static constexpr int N = 2, LAST = 4;
+    using R0 = Round<8, 0xF00>;
+    using R1 = Round<4, 0x0F0>;
+};
 
 template <typename G, int LO>
 __device__ __forceinline__ uint32_t tile_elem(uint32_t tid, uint32_t r) {
@@ -106,6 +153,22 @@ __device__ __forceinline__ void bfly(V &a, V &b, R A, R B) {
     b = nb;
 }
 
+// Butterflies on the register bits of mapping LO that are in MASK and active.
+template <typename G, bool UA, int LO, uint32_t MASK>
+__device__ __forceinline__ void mask_butterflies(typename G::V *v, uint32_t active, typename G::Real A,
+                                                 typename G::Real B) {
+    constexpr int RB = G::RB;
+    constexpr int NR = 1 << RB;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+        if (((MASK >> (LO + q)) & 1u) && ((active >> (LO + q)) & 1u)) {
+#pragma unroll
+            for (int i = 0; i < NR; ++i)
+                if (!(i & (1 << q))) bfly<UA>(v[i], v[i | (1 << q)], A, B);
+        }
+    }
+}
+
 // Butterflies on the register bits of mapping LO whose tile bits are in `mask`
 // (bits LO + q, q = 0..RB-1) and below `below` (compile-time exclusion of bits
 // done in an earlier round).
@@ -144,14 +207,15 @@ __device__ __forceinline__ void exchange(typename G::V *v, typename G::V *tile) 
     for (int r = 0; r < NR; ++r) v[r] = tile[bt ^ G::swz((uint32_t)r << TO)];
 }
 
-// FP64 block reduction of NV values per thread; thread 0 gets the sums.
-template <int NV>
+// FP64 block reduction of NV values per thread (NT threads); thread 0 gets
+// the sums.
+template <int NV, int NT = PT>
 __device__ __forceinline__ void block_sum(double (&x)[NV]) {
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x[k] += __shfl_xor_sync(0xFFFFFFFFu, x[k], o);
-    __shared__ double s_red[PT / 32][NV];
+    __shared__ double s_red[NT / 32][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0)
@@ -162,7 +226,7 @@ __device__ __forceinline__ void block_sum(double (&x)[NV]) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double s = 0.0;
-            for (int w = 0; w < PT / 32; ++w) s += s_red[w][k];
+            for (int w = 0; w < NT / 32; ++w) s += s_red[w][k];
             x[k] = s;
         }
     }
