@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
     constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tp = reinterpret_cast<V *>(smem_raw);
-    V *tl = tp + (1 << T);
-    V *stab = tl + (1 << T);
+    V *tl = tp + G::TILE_ELEMS;
+    V *stab = tl + G::TILE_ELEMS;
     if (LOW) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
             V z;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(PT) small_grad_kernel(const uint8_t *costs, in
 
 template <typename R>
 static size_t adj_smem(int m) {
-    return sizeof(typename AGeo<R>::V) * (2 * (size_t(1) << AGeo<R>::T) + (m < 0 ? 0 : (size_t)(m < 255 ? 256 : m + 1)));
+    return sizeof(typename AGeo<R>::V) * (2 * (size_t)AGeo<R>::TILE_ELEMS + (m < 0 ? 0 : (size_t)(m < 255 ? 256 : m + 1)));
 }
 
 template <typename R>

@@ -199,14 +199,14 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     cp_async_commit();
     for (int i = 0; t < a.tiles; ++i, t += gridDim.x) {
         const int b = i & 1;
-        V *tile = bufs + ((size_t)b << T);
+        V *tile = bufs + (size_t)b * G::TILE_ELEMS;
         uint8_t *sc = scs + ((size_t)b << T);
         const uint64_t base = tile_base(t, a.row, a.lo, T);
         // prefetch the next tile into the other buffer while this one computes
         const uint64_t tn = t + gridDim.x;
         if (tn < a.tiles)
             issue_tile<R, LOW>(st, cs, tile_base(tn, a.row, a.lo, T), a.row, a.lo, need_s, need_c,
-                               bufs + ((size_t)(b ^ 1) << T), scs + ((size_t)(b ^ 1) << T));
+                               bufs + (size_t)(b ^ 1) * G::TILE_ELEMS, scs + ((size_t)(b ^ 1) << T));
         cp_async_commit();
         cp_async_wait_prev();  // this tile's copies (all but the newest group) are done
         __syncthreads();
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 1) pass_kernel(const __grid_constan
     constexpr int T = Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *bufs = reinterpret_cast<V *>(smem_raw);
-    uint8_t *scs = reinterpret_cast<uint8_t *>(bufs + (2 << T));
+    uint8_t *scs = reinterpret_cast<uint8_t *>(bufs + 2 * Cx<R>::TILE_ELEMS);
     V *stab = reinterpret_cast<V *>(scs + (2 << T));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) {
@@ -455,7 +455,8 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 template <typename R>
 static size_t pass_smem(bool phase, int m) {
     const size_t T = size_t(1) << Cx<R>::T;
-    return 2 * sizeof(typename Cx<R>::V) * T + 2 * T + (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
+    return 2 * sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS + 2 * T +
+           (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
 template <typename R>

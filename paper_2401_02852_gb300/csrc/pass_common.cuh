@@ -44,18 +44,22 @@ struct Geo {
     static constexpr int LOAD = TB;
     static constexpr int LC_LOW = RB_;  // adjoint passes: rounds at 8, 0, RB
     static constexpr int LC_HIGH = 4;
-    static constexpr int SW_SHIFT = RB_;
-    static constexpr uint32_t SW_MASK = sizeof(R) == 4 ? 15u : 7u;
-    __device__ static __forceinline__ uint32_t swz(uint32_t u) { return u ^ ((u >> SW_SHIFT) & SW_MASK); }
+    // Padded layout: one spare amplitude after every 2^RB, which keeps every
+    // mapping used free of bank conflicts.  It is additive over the disjoint
+    // thread and register bit fields of a tile element, so an exchange address
+    // is a per-thread base plus a compile-time offset.
+    static constexpr int PADSH = RB_;
+    static constexpr int TILE_ELEMS = (1 << T_) + (1 << (T_ - RB_));
+    __host__ __device__ static constexpr uint32_t swz(uint32_t u) { return u + (u >> PADSH); }
 };
 
-// Forward geometry: 64 KiB tiles; complex64 with 512 threads x 16 amplitudes,
-// complex128 with 256 threads x 16 amplitudes.
+// Forward geometry: 64 KiB tiles, 256 threads; complex64 with 32 amplitudes
+// per thread, complex128 with 16.
 template <typename R>
 struct FwdGeoT;
 template <>
 struct FwdGeoT<float> {
-    using type = Geo<float, 13, 4>;
+    using type = Geo<float, 13, 5>;
 };
 template <>
 struct FwdGeoT<double> {
@@ -78,19 +82,17 @@ struct Round {
 template <typename G, bool LOW>
 struct PassRounds;
 template <>
-struct PassRounds<Geo<float, 13, 4>, true> {
-    static constexpr int N = 4, LAST = 5;
-    using R0 = Round<9, 0x1E00>;
-    using R1 = Round<0, 0x000F>;
-    using R2 = Round<4, 0x00F0>;
-    using R3 = Round<5, 0x0100>;
+struct PassRounds<Geo<float, 13, 5>, true> {
+    static constexpr int N = 3, LAST = 5;
+    using R0 = Round<8, 0x1F00>;
+    using R1 = Round<0, 0x001F>;
+    using R2 = Round<5, 0x00E0>;
 };
 template <>
-struct PassRounds<Geo<float, 13, 4>, false> {
-    static constexpr int N = 3, LAST = 5;
-    using R0 = Round<9, 0x1E00>;
+struct PassRounds<Geo<float, 13, 5>, false> {
+    static constexpr int N = 2, LAST = 4;
+    using R0 = Round<8, 0x1F00>;
     using R1 = Round<4, 0x00F0>;
-    using R2 = Round<5, 0x0100>;
 };
 template <>
 struct PassRounds<Geo<double, 12, 4>, true> {
@@ -187,24 +189,24 @@ __device__ __forceinline__ void reg_butterflies(typename G::V *v, uint32_t mask,
     }
 }
 
-// Re-distribute the tile from mapping FROM to mapping TO through shared memory.
-// The swizzle is linear over XOR and the thread and register parts of a tile
-// element have disjoint bits, so swz(u) = swz(thread part) ^ swz(r << LO), the
-// second term a compile-time constant: one LOP3 per access.  The thread parts
-// pass through an opaque asm so that the compiler recomputes addresses per
-// tile instead of hoisting (and spilling) all of them out of the tile loop.
+// Re-distribute the tile from mapping FROM to mapping TO through shared memory
+// (padded layout: per-thread base + compile-time offset per register).  The
+// thread parts pass through an opaque asm so that the compiler recomputes them
+// per tile instead of hoisting them out of the tile loop.
 template <typename G, int FROM, int TO>
 __device__ __forceinline__ void exchange(typename G::V *v, typename G::V *tile) {
     constexpr int NR = G::NR;
     const uint32_t tid = threadIdx.x;
     uint32_t bf = G::swz(tile_elem<G, FROM>(tid, 0)), bt = G::swz(tile_elem<G, TO>(tid, 0));
     asm volatile("" : "+r"(bf), "+r"(bt));
+    typename G::V *pf = tile + bf;
+    typename G::V *pt = tile + bt;
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) tile[bf ^ G::swz((uint32_t)r << FROM)] = v[r];
+    for (int r = 0; r < NR; ++r) pf[G::swz((uint32_t)r << FROM)] = v[r];
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = tile[bt ^ G::swz((uint32_t)r << TO)];
+    for (int r = 0; r < NR; ++r) v[r] = pt[G::swz((uint32_t)r << TO)];
 }
 
 // FP64 block reduction of NV values per thread (NT threads); thread 0 gets
