@@ -54,28 +54,36 @@ struct LastLO {
     static constexpr int value = PassRounds<G, LOW>::LAST;
 };
 
-// The rounds of one layer from the load mapping to the last mapping...
-template <typename G, bool LOW, bool UA>
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// The rounds of one layer from the load mapping to the last mapping...  `hook`
+// runs right after the last exchange (the tile buffer is free from then on).
+template <typename G, bool LOW, bool UA, class Hook>
 __device__ __forceinline__ void rounds_up(typename G::V *v, typename G::V *tile, uint32_t active, typename G::Real A,
-                                          typename G::Real B) {
+                                          typename G::Real B, const Hook &hook) {
     using P = PassRounds<G, LOW>;
     mask_butterflies<G, UA, P::R0::LO, P::R0::MASK>(v, active, A, B);
     exchange<G, P::R0::LO, P::R1::LO>(v, tile);
+    if constexpr (P::N == 2) hook();
     mask_butterflies<G, UA, P::R1::LO, P::R1::MASK>(v, active, A, B);
     if constexpr (P::N > 2) {
         exchange<G, P::R1::LO, P::R2::LO>(v, tile);
+        if constexpr (P::N == 3) hook();
         mask_butterflies<G, UA, P::R2::LO, P::R2::MASK>(v, active, A, B);
     }
     if constexpr (P::N > 3) {
         exchange<G, P::R2::LO, P::R3::LO>(v, tile);
+        hook();
         mask_butterflies<G, UA, P::R3::LO, P::R3::MASK>(v, active, A, B);
     }
 }
 
 // ... and back from the last mapping to the load mapping (same qubits).
-template <typename G, bool LOW, bool UA>
+template <typename G, bool LOW, bool UA, class Hook>
 __device__ __forceinline__ void rounds_down(typename G::V *v, typename G::V *tile, uint32_t active,
-                                            typename G::Real A, typename G::Real B) {
+                                            typename G::Real A, typename G::Real B, const Hook &hook) {
     using P = PassRounds<G, LOW>;
     if constexpr (P::N > 3) {
         mask_butterflies<G, UA, P::R3::LO, P::R3::MASK>(v, active, A, B);
@@ -87,6 +95,7 @@ __device__ __forceinline__ void rounds_down(typename G::V *v, typename G::V *til
     }
     mask_butterflies<G, UA, P::R1::LO, P::R1::MASK>(v, active, A, B);
     exchange<G, P::R1::LO, P::R0::LO>(v, tile);
+    hook();
     mask_butterflies<G, UA, P::R0::LO, P::R0::MASK>(v, active, A, B);
 }
 
@@ -131,7 +140,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Issues the copies of tile `base` into (buf, sc): the state as 16-byte chunks
 // (the tile's rows of 2^row amplitudes are whole numbers of chunks) and, when
@@ -172,7 +181,7 @@ __device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const ui
 
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
-                                           typename Cx<R>::V *bufs, uint8_t *scs) {
+                                           typename Cx<R>::V *tile, uint8_t *scs) {
     using G = Cx<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
@@ -195,20 +204,24 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     uint64_t t = blockIdx.x;
     if (t < a.tiles)
-        issue_tile<R, LOW>(st, cs, tile_base(t, a.row, a.lo, T), a.row, a.lo, need_s, need_c, bufs, scs);
+        issue_tile<R, LOW>(st, cs, tile_base(t, a.row, a.lo, T), a.row, a.lo, need_s, need_c, tile, scs);
     cp_async_commit();
     for (int i = 0; t < a.tiles; ++i, t += gridDim.x) {
         const int b = i & 1;
-        V *tile = bufs + (size_t)b * G::TILE_ELEMS;
         uint8_t *sc = scs + ((size_t)b << T);
         const uint64_t base = tile_base(t, a.row, a.lo, T);
-        // prefetch the next tile into the other buffer while this one computes
         const uint64_t tn = t + gridDim.x;
-        if (tn < a.tiles)
-            issue_tile<R, LOW>(st, cs, tile_base(tn, a.row, a.lo, T), a.row, a.lo, need_s, need_c,
-                               bufs + (size_t)(b ^ 1) * G::TILE_ELEMS, scs + ((size_t)(b ^ 1) << T));
-        cp_async_commit();
-        cp_async_wait_prev();  // this tile's copies (all but the newest group) are done
+        // Once the tile's last exchange is read out the buffer is free: copy the
+        // next tile into it (and its cost bytes into the other cost buffer)
+        // while this tile finishes its last round and its stores.
+        auto prefetch = [&]() {
+            __syncthreads();
+            if (tn < a.tiles)
+                issue_tile<R, LOW>(st, cs, tile_base(tn, a.row, a.lo, T), a.row, a.lo, need_s, need_c, tile,
+                                   scs + ((size_t)(b ^ 1) << T));
+            cp_async_commit();
+        };
+        cp_async_wait_all();  // this tile's copies are done
         __syncthreads();
         V v[NR];
 #pragma unroll
@@ -221,16 +234,16 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
             else
                 v[r] = tile[u];
         }
-        rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1);
         if (MODE == MODE_FUSED) {
+            rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1, NoHook());
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
-            rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2);
+            rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2, prefetch);
             store_tile<R, LD>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce, acc);
         } else {
+            rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1, prefetch);
             store_tile<R, LC>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce, acc);
         }
-        __syncthreads();  // every thread is done with this buffer before it is refilled
     }
     if (a.reduce) {
         block_sum<2, G::PT>(acc);
@@ -249,18 +262,18 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
     return (e + 15) & ~15;
 }
 
-// One CTA per SM, persistent over tiles, double-buffered: two state buffers,
-// two cost-byte buffers, then the phase table.
+// Two CTAs per SM, persistent over tiles: one (padded) tile buffer, two
+// cost-byte buffers, then the phase table.
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT>
-__global__ void __launch_bounds__(Cx<R>::PT, 1) pass_kernel(const __grid_constant__ PassArgs<R> a,
+__global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                             const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
     constexpr int T = Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *bufs = reinterpret_cast<V *>(smem_raw);
-    uint8_t *scs = reinterpret_cast<uint8_t *>(bufs + 2 * Cx<R>::TILE_ELEMS);
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    uint8_t *scs = reinterpret_cast<uint8_t *>(tile + Cx<R>::TILE_ELEMS);
     V *stab = reinterpret_cast<V *>(scs + (2 << T));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) {
@@ -270,7 +283,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 1) pass_kernel(const __grid_constan
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, bufs, scs);
+    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, tile, scs);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -450,12 +463,12 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 // ---------------------------------------------------------------------------
 // Host side of the multi-pass evolution.
 
-// Dynamic shared memory of a pass: two tile buffers, two cost-byte buffers and
+// Dynamic shared memory of a pass: the tile buffer, two cost-byte buffers and
 // the phase table (modes that apply a phase).
 template <typename R>
 static size_t pass_smem(bool phase, int m) {
     const size_t T = size_t(1) << Cx<R>::T;
-    return 2 * sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS + 2 * T +
+    return sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS + 2 * T +
            (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
@@ -528,7 +541,7 @@ int pass_grid_x(int dtype, int n, int batch) {
     DeviceInfo di;
     if (device_info(&di)) return -1;
     const int T = dtype == QAOA_C64 ? Cx<float>::T : Cx<double>::T;
-    return grid_x(di.sms, 1, batch, 1ull << (n - T));  // one persistent CTA per SM
+    return grid_x(di.sms, 2, batch, 1ull << (n - T));  // two persistent CTAs per SM
 }
 
 template <typename R>
