@@ -305,6 +305,11 @@ def run_native(args, ws, rank, local):
                          "c64_speedup_over_c128": ms128 / (ms / args.steps - 0.0)}
         del st128
 
+    if args.serve_requests > 0 and rank == 0 and ws == 1:
+        from paper_2401_02852_gb300 import workloads
+        torch.cuda.empty_cache()
+        extra["serving"] = workloads.serve_workload(count=args.serve_requests, rate_hz=200.0)
+
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -323,6 +328,29 @@ def run_native(args, ws, rank, local):
     return 0
 
 
+def run_workload(args):
+    """The other configured workloads: one JSON line each (not the headline)."""
+    import torch
+
+    from paper_2401_02852_gb300 import workloads
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    if args.workload == "serve":
+        res = workloads.serve_workload(count=args.requests, rate_hz=args.rate)
+    elif args.workload == "grad":
+        res = workloads.grad_workload(batch=args.batch, n=args.grad_n, p=args.grad_p, adam_steps=args.adam_steps)
+    elif args.workload == "sweep":
+        res = workloads.sweep_workload(ns=range(args.sweep_n0, args.sweep_n1 + 1, 2), seeds=args.seeds,
+                                       out_dir=args.out_dir)
+    else:
+        res = workloads.batch_workload()
+    res["workload"] = args.workload
+    res["wall_seconds"] = time.perf_counter() - t0
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,10 +363,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-c128", dest="compare_c128", action="store_false")
+    ap.add_argument("--serve-requests", type=int, default=1500,
+                    help="short serving run (Poisson 200/s) reported beside the headline; 0 skips it")
+    ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch"], default="evolve")
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--grad-n", type=int, default=22)
+    ap.add_argument("--grad-p", type=int, default=20)
+    ap.add_argument("--adam-steps", type=int, default=200)
+    ap.add_argument("--sweep-n0", type=int, default=16)
+    ap.add_argument("--sweep-n1", type=int, default=32)
+    ap.add_argument("--seeds", type=int, default=200)
+    ap.add_argument("--out-dir", default=None)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload != "evolve":
+        return run_workload(args)
     return run_native(args, ws, rank, local)
 
 

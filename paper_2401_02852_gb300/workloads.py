@@ -1,0 +1,134 @@
+"""Benchmark workloads beyond the headline evolution (driven by ``bench.py``).
+
+* ``serve``:  a Poisson stream of NAE-5-SAT requests (n ~ U{14..26},
+  p ~ U{1..20}, r = 8, linear ramps) through the native serving loop, against
+  one request per launch on the same GPU;
+* ``grad``:   batched adjoint gradients (256 instances, n = 22, p = 20) checked
+  against central differences, then Adam on the shared angles;
+* ``sweep``:  median 1/p_succ versus n and its fitted exponent;
+* ``batch``:  100 small instances (n = 12, p = 5, complex128) in one launch.
+
+Every function returns a JSON-serialisable dict.  All device work goes through
+the library's C ABI.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import api, serve, sweep, train
+from . import instances as gen
+
+
+def _sync():
+    torch.cuda.synchronize()
+
+
+def serve_workload(count: int = 20000, rate_hz: float = 200.0, n_range=(14, 26), p_range=(1, 20),
+                   n_streams: int = 4, seed: int = 0, baseline: bool = True) -> dict:
+    reqs = gen.serving_requests(count, rate_hz=rate_hz, n_range=n_range, p_range=p_range, seed=seed)
+    warm = gen.serving_requests(16, rate_hz=1e6, n_range=n_range, p_range=p_range, seed=seed + 1)
+    with serve.Server("c64", n_streams=n_streams) as s:
+        for rq in warm:
+            s.wait(s.submit(rq.instance, rq.gamma, rq.beta))
+        res, wall = serve.replay(s, reqs)
+        stats = s.stats()
+    lat = np.array([r.latency_s for r in res])
+    amp_layers = sum((1 << rq.instance.n) * rq.p for rq in reqs)
+    out = {"requests": count, "rate_hz": rate_hz, "n_range": list(n_range), "p_range": list(p_range),
+           "server": serve.latency_summary(lat, wall, count) | {"amp_layer_per_s": amp_layers / wall},
+           "server_stats": stats, "errors": int(sum(r.status != 0 for r in res))}
+    if baseline:
+        work = {}
+        for rq in warm:
+            api.psucc_host(rq.instance, rq.gamma, rq.beta, "c64", work=work)
+        base_ps, base_lat, base_wall = serve.one_per_launch(reqs)
+        out["one_per_launch"] = serve.latency_summary(base_lat, base_wall, count)
+        ps = np.array([r.p_succ for r in res])
+        bp = np.array(base_ps)
+        mask = bp > 0
+        out["max_rel_diff_vs_one_per_launch"] = float(np.max(np.abs(ps[mask] - bp[mask]) / bp[mask])) if mask.any() else 0.0
+        out["speedup_inst_per_s"] = out["server"]["inst_per_s"] / out["one_per_launch"]["inst_per_s"]
+        out["p99_ratio"] = out["one_per_launch"]["p99_ms"] / out["server"]["p99_ms"]
+    return out
+
+
+def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 200, lr: float = 0.01,
+                  fd_instances: int = 2, seed_tag: str = "grad-cfg", checkpoint=None) -> dict:
+    m = gen.clause_count(n, 8.0)
+    insts = []
+    for i in range(batch):
+        inst, _ = gen.satisfiable_instance(seed_tag, n, 5, 8.0, i, lambda x: api.cost_table(x)[1])
+        insts.append(inst)
+    costs, _, _ = api.cost_table_batch(insts)
+    g0, b0 = gen.linear_ramp(p)
+    work = (torch.empty((batch, 1 << n), dtype=torch.complex64, device="cuda"),
+            torch.empty((batch, 1 << n), dtype=torch.complex64, device="cuda"))
+    api.grad_batch(n, costs, m, g0, b0, "c64", work=work)  # warm-up
+    _sync()
+    t0 = time.perf_counter()
+    ps, dg, db = api.grad_batch(n, costs, m, g0, b0, "c64", work=work)
+    _sync()
+    t_grad = time.perf_counter() - t0
+    # central differences (h = 1e-4) on the complex128 evolution of a few instances
+    fd = []
+    h = 1e-4
+    for i in range(fd_instances):
+        c = costs[i].contiguous()
+        ps128, dg128, db128 = api.grad(n, c, m, g0, b0, "c128")
+        f = lambda gg, bb: api.evolve(n, c, m, gg, bb, "c128")[1]
+        err_g, err_b, scale = 0.0, 0.0, max(np.max(np.abs(dg128)), np.max(np.abs(db128)))
+        for l in range(p):
+            e = np.zeros(p)
+            e[l] = h
+            fdg = (f(g0 + e, b0) - f(g0 - e, b0)) / (2 * h)
+            fdb = (f(g0, b0 + e) - f(g0, b0 - e)) / (2 * h)
+            err_g = max(err_g, abs(fdg - dg128[l]))
+            err_b = max(err_b, abs(fdb - db128[l]))
+        fd.append({"instance": i, "c128_vs_fd_max_abs_over_max_grad": max(err_g, err_b) / scale,
+                   "c64_vs_c128_max_abs_over_max_grad": float(max(np.max(np.abs(dg[i] - dg128)),
+                                                                  np.max(np.abs(db[i] - db128))) / scale),
+                   "c64_psucc_rel_err_vs_c128": abs(ps[i] - ps128) / ps128})
+    del work
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    g1, b1, trace = train.train_angles(costs, n, m, g0, b0, steps=adam_steps, lr=lr, checkpoint=checkpoint)
+    _sync()
+    t_adam = time.perf_counter() - t0
+    # one gradient = forward (p layers) + reverse sweep (p layers on two states)
+    amp_layers = batch * (1 << n) * p
+    return {"batch": batch, "n": n, "m": m, "p": p, "grad_seconds": t_grad,
+            "grad_amp_layer_per_s_forward_equiv": amp_layers / t_grad, "mean_psucc_initial": float(np.mean(ps)),
+            "fd_checks": fd, "adam_steps": adam_steps, "adam_seconds": t_adam,
+            "objective_first": trace[0][1], "objective_last": trace[-1][1],
+            "trace_every_20": [t for t in trace if t[0] % 20 == 0 or t[0] == len(trace) - 1],
+            "gamma_final": list(map(float, g1)), "beta_final": list(map(float, b1))}
+
+
+def sweep_workload(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, out_dir=None) -> dict:
+    res = sweep.run_sweep(ns=ns, ps=ps, seeds=seeds, out_dir=out_dir, log=None)
+    table = {f"n{n}_p{p}": r["median_inv_psucc"] for (n, p), r in sorted(res["results"].items())}
+    return {"seeds": seeds, "ns": list(ns), "ps": list(ps), "median_inv_psucc": table,
+            "fits_bits": {str(p): {"c": f["c_bits"], "d": f["d"]} for p, f in res["fits"].items()},
+            "random_assignment_bits": res["random_assignment_bits"],
+            "amp_layer_per_s": res["amp_layer_per_s"], "gpu_seconds": res["gpu_seconds"]}
+
+
+def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p: int = 5, reps: int = 20) -> dict:
+    insts = [gen.satisfiable_instance("batch-cfg", n, k, r, i, lambda x: api.cost_table(x)[1])[0]
+             for i in range(count)]
+    costs, sols, _ = api.cost_table_batch(insts)
+    g, b = gen.linear_ramp(p)
+    states = torch.empty((count, 1 << n), dtype=torch.complex128, device="cuda")
+    api.evolve_batch(n, costs, insts[0].m, g, b, "c128", out=states)
+    _sync()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, ps, nm = api.evolve_batch(n, costs, insts[0].m, g, b, "c128", out=states)
+    _sync()
+    dt = (time.perf_counter() - t0) / reps
+    return {"count": count, "n": n, "m": insts[0].m, "p": p, "ms_per_batch": dt * 1e3,
+            "amp_layer_per_s": count * (1 << n) * p / dt, "mean_psucc": float(np.mean(ps)),
+            "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols))}
