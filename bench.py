@@ -243,12 +243,10 @@ def run_native(args, ws, rank, local):
         barrier()
     launches = api.launch_count() - launches0
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * (2 ** n) * p * args.steps / (ms_max / 1000.0)
+    from paper_2401_02852_gb300 import dist as qdist  # replicas: only scalars cross ranks
+    dev = "cuda" if dist is not None else "cpu"
+    ms_max = 1000.0 * qdist.max_over_ranks(ms / 1000.0, device=dev)
+    value = qdist.job_throughput(float((2 ** n) * p * args.steps), ms / 1000.0, device=dev)
 
     # roofline of the dominant kernel from the live per-launch events
     kinds = prof.stats
