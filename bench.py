@@ -284,6 +284,32 @@ def run_native(args, ws, rank, local):
     extra = {"p_succ": results["p_succ"], "norm": results["norm"], "n_sol": n_sol, "m": inst.m,
              "passes_per_layer": len(plan), "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kinds.items()},
              "pass_ms_per_step": pass_ms, "effective_GBps_at_17B": effective if es == 8 else None}
+    if args.z2 and rank == 0:
+        # the halved state (exact by the global-flip symmetry): same p_succ, half the bytes
+        from paper_2401_02852_gb300._lib import Z2_HALF
+        half = torch.empty(1 << (n - 1), dtype=torch.uint8, device="cuda")
+        st_h = torch.empty(1 << (n - 1), dtype=state.dtype, device="cuda")
+        hres = {}
+
+        def step_h():
+            api.cost_table_half(inst, out=half, stats=False)
+            _, hres["p"], hres["nm"] = api.evolve(n, half, inst.m, g, b, dtype, flags=Z2_HALF, out=st_h)
+
+        for _ in range(3):
+            step_h()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(args.steps):
+            step_h()
+        a1.record()
+        torch.cuda.synchronize()
+        ms_h = a0.elapsed_time(a1) / args.steps
+        extra["z2_halved"] = {"ms_per_step": ms_h, "amp_layer_per_s": (2 ** n) * p / (ms_h / 1000.0),
+                              "p_succ": hres["p"], "p_succ_rel_diff_vs_full": abs(hres["p"] - results["p_succ"]) /
+                              results["p_succ"], "stored_state_GB": (2 ** (n - 1)) * es / 1e9}
+        del half, st_h
+
     if args.compare_c128 and dtype == "c64" and rank == 0:
         del state
         torch.cuda.empty_cache()
@@ -361,6 +387,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-c128", dest="compare_c128", action="store_false")
+    ap.add_argument("--no-z2", dest="z2", action="store_false", help="skip the halved-state measurement")
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="short serving run (Poisson 200/s) reported beside the headline; 0 skips it")
     ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch"], default="evolve")

@@ -63,6 +63,15 @@ extern "C" {
 #define QAOA_MIXER_PAPER 0x0
 #define QAOA_MIXER_RX2B 0x1
 
+/* Halved state.  NAE-SAT is symmetric under the global bit flip (Sec. 2.2):
+ * C(x) = C(not x), and |+>, U_C and U_B commute with the flip, so
+ * psi(x) = psi(not x) at every layer.  With QAOA_Z2_HALF the state buffer holds
+ * only the 2^(n-1) amplitudes with bit n-1 clear and the cost table only
+ * C(x) for those x (naesat_cost_table_half); the mixer's factor on qubit n-1
+ * then pairs x with 2^(n-1) - 1 - x.  Results (p_succ, norm) are those of the
+ * full state.  Exact: the same numbers as the full evolution, half the bytes. */
+#define QAOA_Z2_HALF 0x2
+
 #define QAOA_MAX_N 32
 #define QAOA_MAX_M 1023
 
@@ -98,6 +107,13 @@ int qaoa_release_scratch(void);
  * Synchronises the stream when n_sol or max_cost is requested. */
 int naesat_cost_table(const naesat_instance *inst, uint8_t *d_cost, uint64_t *n_sol,
                       uint32_t *max_cost, void *stream);
+
+/* Half table for the QAOA_Z2_HALF mode: C(x) for x in [0, 2^(n-1)) only
+ * (d_cost_half device uint8 [2^(n-1)], n >= 6).  C(not x) = C(x) under NAE, so
+ * this determines the full table; n_sol and max_cost are those of the full
+ * table (n_sol = 2 x the half count).  Same errors as naesat_cost_table. */
+int naesat_cost_table_half(const naesat_instance *inst, uint8_t *d_cost_half, uint64_t *n_sol,
+                           uint32_t *max_cost, void *stream);
 
 /* Same for `batch` instances of one n: d_costs is device uint8 [batch][2^n];
  * n_sol / max_cost are host arrays [batch] (nullable). */
@@ -193,7 +209,8 @@ typedef struct {
     int n_streams;           /* CUDA streams for large requests (0 = 4)                       */
     int dtype;               /* QAOA_C64 or QAOA_C128                                          */
     int small_n_max;         /* n at or below which requests are packed (0 = default)         */
-    int flags;               /* mixer sign flags, as for qaoa_evolve                           */
+    int flags;               /* mixer sign flags as for qaoa_evolve; QAOA_Z2_HALF runs the
+                                unpacked requests on the halved state (half the memory)       */
     int device;              /* CUDA device ordinal                                            */
     int max_n;               /* largest n accepted (0 = 30)                                    */
 } qaoa_server_opts;
@@ -222,13 +239,14 @@ int qaoa_server_stats(qaoa_server *s, uint64_t *counters /* [8] */);
 int qaoa_server_destroy(qaoa_server *s);
 
 /* ---- pass planning and instrumentation (host only, no device work) ----------
- * qaoa_plan describes how one layer of an n-qubit evolution in dtype is split
- * into HBM passes.  Pass 0 streams contiguous tiles and mixes qubits
+ * qaoa_plan describes how one layer of an n-qubit evolution in dtype (and
+ * flags: QAOA_Z2_HALF, where pass 0 mixes qubits [0, T - 1) and qubit n - 1 and
+ * the high passes work on n - 1 index bits) is split into HBM passes.  Pass 0 streams contiguous tiles and mixes qubits
  * [0, row_bits[0]).  Pass i > 0 streams tiles of 2^row_bits[i] contiguous
  * amplitudes times 2^G rows strided by 2^group_lo[i] (G = tile bits -
  * row_bits[i]) and mixes the top group_bits[i] qubits of its group.  Returns
  * the number of passes per layer (>= 1) or an error; arrays hold up to 8. */
-int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits);
+int qaoa_plan(int n, int dtype, int flags, int *group_lo, int *group_bits, int *row_bits);
 
 /* The launch sequence of a depth-p evolution: for launch i, the pass of
  * qaoa_plan it runs, its layer l and its mode (0: first pass of layer 0, which
@@ -239,7 +257,8 @@ int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits);
  * layer boundary on a strided group costs one pass instead of two.  Returns
  * the number of launches (p * (passes - 1) + 1 when every boundary fuses) or
  * an error; at most max_launches entries are written. */
-int qaoa_pass_schedule(int n, int p, int dtype, int max_launches, int *pass_index, int *layer, int *mode);
+int qaoa_pass_schedule(int n, int p, int dtype, int flags, int max_launches, int *pass_index, int *layer,
+                       int *mode);
 
 /* Per-kernel timing: when enabled, every kernel the library launches is
  * bracketed by CUDA events on its stream.  qaoa_profile_read synchronises the

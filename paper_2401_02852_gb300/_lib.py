@@ -18,6 +18,7 @@ QAOA_PENDING = 1
 ERRORS = {-1: "EINVAL", -2: "ERANGE", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ECANCELLED", -7: "ENOTFOUND"}
 C64, C128 = 0, 1
 MIXER_PAPER, MIXER_RX2B = 0, 1
+Z2_HALF = 2
 
 
 class QaoaError(RuntimeError):
@@ -52,6 +53,7 @@ SIGNATURES = {
     "qaoa_version": (I, []),
     "qaoa_release_scratch": (I, []),
     "naesat_cost_table": (I, [P, P, P, P, P]),
+    "naesat_cost_table_half": (I, [P, P, P, P, P]),
     "naesat_cost_table_batch": (I, [I, P, P, P, P, P]),
     "qaoa_evolve": (I, [I, P, I, I, P, P, I, I, P, P, P, P]),
     "qaoa_evolve_batch": (I, [I, I, P, I, I, P, P, I, I, P, P, P, P]),
@@ -66,8 +68,8 @@ SIGNATURES = {
     "qaoa_serve_cancel": (I, [P, ctypes.c_uint64]),
     "qaoa_server_stats": (I, [P, P]),
     "qaoa_server_destroy": (I, [P]),
-    "qaoa_plan": (I, [I, I, P, P, P]),
-    "qaoa_pass_schedule": (I, [I, I, I, I, P, P, P]),
+    "qaoa_plan": (I, [I, I, I, P, P, P]),
+    "qaoa_pass_schedule": (I, [I, I, I, I, I, P, P, P]),
     "qaoa_profile_enable": (I, [I]),
     "qaoa_profile_read": (I, [I, P, P]),
     "qaoa_kernel_name": (ctypes.c_char_p, [I]),

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import C64, C128, MIXER_PAPER, MIXER_RX2B, NaesatInstance, check, load
+from ._lib import C64, C128, MIXER_PAPER, MIXER_RX2B, Z2_HALF, NaesatInstance, check, load
 
 DTYPES = {"c64": C64, "c128": C128, C64: C64, C128: C128, torch.complex64: C64, torch.complex128: C128}
 TORCH_DTYPE = {C64: torch.complex64, C128: torch.complex128}
@@ -73,6 +73,19 @@ def cost_table(inst, out: Optional[torch.Tensor] = None, stream=None, stats: boo
     return out, (int(ns.value) if stats else None), (int(mx.value) if stats else None)
 
 
+def cost_table_half(inst, out: Optional[torch.Tensor] = None, stream=None, stats: bool = True):
+    """C(x) for x < 2^(n-1) (the halved-state table); n_sol / max_cost of the full table."""
+    n = int(inst.n)
+    if out is None:
+        out = torch.empty(1 << (n - 1), dtype=torch.uint8, device="cuda")
+    ci = _Inst(inst)
+    ns = ctypes.c_uint64()
+    mx = ctypes.c_uint32()
+    args = (ctypes.byref(ns), ctypes.byref(mx)) if stats else (None, None)
+    check(load().naesat_cost_table_half(ctypes.byref(ci.s), _ptr(out), *args, _stream(stream)))
+    return out, (int(ns.value) if stats else None), (int(mx.value) if stats else None)
+
+
 def cost_table_batch(insts: Sequence, out: Optional[torch.Tensor] = None, stream=None):
     """Cost tables of several instances of one n: uint8 [B, 2^n], n_sol [B], max [B]."""
     B = len(insts)
@@ -92,13 +105,15 @@ def evolve(n: int, cost: torch.Tensor, m: int, gamma, beta, dtype="c64", flags: 
     """prod_l U_B(beta_l) U_C(gamma_l) |+>^n; returns (state, p_succ, norm).
 
     ``want=False`` skips the fused reduction and does not wait for the device.
+    With ``flags & Z2_HALF`` the state holds the 2^(n-1) amplitudes with bit
+    n-1 clear and ``cost`` is the half table (``cost_table_half``).
     """
     code = dtype_code(dtype)
     g, b = _f64(gamma), _f64(beta)
     if g.shape != b.shape:
         raise ValueError("gamma and beta differ in length")
     if out is None:
-        out = torch.empty(1 << n, dtype=TORCH_DTYPE[code], device="cuda")
+        out = torch.empty(1 << (n - 1 if flags & Z2_HALF else n), dtype=TORCH_DTYPE[code], device="cuda")
     ps, nm = ctypes.c_double(), ctypes.c_double()
     res = (ctypes.byref(ps), ctypes.byref(nm)) if want else (None, None)
     check(load().qaoa_evolve(n, _ptr(cost), int(m), g.shape[0], _np_ptr(g), _np_ptr(b), code, flags, _ptr(out),
@@ -113,7 +128,7 @@ def evolve_batch(n: int, costs: torch.Tensor, m_max: int, gamma, beta, dtype="c6
     B = int(costs.shape[0])
     g, b = _f64(gamma), _f64(beta)
     if out is None:
-        out = torch.empty((B, 1 << n), dtype=TORCH_DTYPE[code], device="cuda")
+        out = torch.empty((B, 1 << (n - 1 if flags & Z2_HALF else n)), dtype=TORCH_DTYPE[code], device="cuda")
     ps = np.zeros(B)
     nm = np.zeros(B)
     check(load().qaoa_evolve_batch(B, n, _ptr(costs), int(m_max), g.shape[0], _np_ptr(g), _np_ptr(b), code, flags,
@@ -184,22 +199,22 @@ def psucc_host(inst, gamma, beta, dtype="c64", flags: int = MIXER_PAPER, work: O
     return ps, nm
 
 
-def plan(n: int, dtype="c64"):
+def plan(n: int, dtype="c64", flags: int = 0):
     """Pass plan: list of (group_lo, group_bits, row_bits) per HBM pass of one layer."""
     lo = (ctypes.c_int * 8)()
     bits = (ctypes.c_int * 8)()
     row = (ctypes.c_int * 8)()
-    k = check(load().qaoa_plan(n, dtype_code(dtype), lo, bits, row))
+    k = check(load().qaoa_plan(n, dtype_code(dtype), flags, lo, bits, row))
     return [(lo[i], bits[i], row[i]) for i in range(k)]
 
 
-def pass_schedule(n: int, p: int, dtype="c64"):
+def pass_schedule(n: int, p: int, dtype="c64", flags: int = 0):
     """Launch sequence of an evolution: list of (pass index, layer, mode)."""
     cap = max(1, p * 8 + 1)
     idx = (ctypes.c_int * cap)()
     lay = (ctypes.c_int * cap)()
     mod = (ctypes.c_int * cap)()
-    k = check(load().qaoa_pass_schedule(n, p, dtype_code(dtype), cap, idx, lay, mod))
+    k = check(load().qaoa_pass_schedule(n, p, dtype_code(dtype), flags, cap, idx, lay, mod))
     return [(idx[i], lay[i], mod[i]) for i in range(k)]
 
 

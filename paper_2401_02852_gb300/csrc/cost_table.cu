@@ -322,13 +322,15 @@ int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d
 }
 
 int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned long long *d_stats,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, bool half) {
     std::vector<char> buf(sizeof(CostParams));
     CostParams *prm = reinterpret_cast<CostParams *>(buf.data());
-    prm->n = inst->n;
+    // the kernel uses n only for the number of assignments: the half table is
+    // the first 2^(n-1) of them (variable n - 1 is 0 there)
+    prm->n = half ? inst->n - 1 : inst->n;
     prm->m = inst->m;
     encode_instance(inst, prm->rec);
-    const uint64_t words = inst->n >= 5 ? (1ull << (inst->n - 5)) : 1ull;
+    const uint64_t words = prm->n >= 5 ? (1ull << (prm->n - 5)) : 1ull;
     const int gx = grid_for(words, 1);
     if (gx < 0) return QAOA_ECUDA;
     profile_before(K_COST_TABLE, stream);
@@ -340,27 +342,38 @@ int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned
 
 using namespace qaoa;
 
-extern "C" int naesat_cost_table(const naesat_instance *inst, uint8_t *d_cost, uint64_t *n_sol, uint32_t *max_cost,
-                                 void *stream_) {
+static int cost_table_common(const naesat_instance *inst, uint8_t *d_cost, uint64_t *n_sol, uint32_t *max_cost,
+                             void *stream_, bool half) {
     int rc = validate_instance(inst);
     if (rc) return rc;
     if (!d_cost) return set_error(QAOA_EINVAL, "d_cost is NULL");
+    if (half && inst->n < 6) return set_error(QAOA_ERANGE, "half table needs n >= 6 (n=%d)", inst->n);
     cudaStream_t stream = (cudaStream_t)stream_;
     Scratch *sc = nullptr;
     rc = scratch_for(stream, 64, 64, &sc);
     if (rc) return rc;
     unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(sc->dev);
     QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 2 * sizeof(unsigned long long), stream));
-    rc = launch_cost_table_one(inst, d_cost, d_stats, stream);
+    rc = launch_cost_table_one(inst, d_cost, d_stats, stream, half);
     if (rc) return rc;
     if (!n_sol && !max_cost && inst->m <= 255) return QAOA_OK;
     unsigned long long *h = reinterpret_cast<unsigned long long *>(sc->host);
     QAOA_CUDA_TRY(cudaMemcpyAsync(h, d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
     QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (n_sol) *n_sol = h[0];
+    if (n_sol) *n_sol = half ? 2 * h[0] : h[0];  // C(not x) = C(x): each half solution has its complement
     if (max_cost) *max_cost = (uint32_t)h[1];
     if (h[1] > 255) return set_error(QAOA_ERANGE, "max C = %llu does not fit the uint8 table", h[1]);
     return QAOA_OK;
+}
+
+extern "C" int naesat_cost_table(const naesat_instance *inst, uint8_t *d_cost, uint64_t *n_sol, uint32_t *max_cost,
+                                 void *stream) {
+    return cost_table_common(inst, d_cost, n_sol, max_cost, stream, false);
+}
+
+extern "C" int naesat_cost_table_half(const naesat_instance *inst, uint8_t *d_cost_half, uint64_t *n_sol,
+                                      uint32_t *max_cost, void *stream) {
+    return cost_table_common(inst, d_cost_half, n_sol, max_cost, stream, true);
 }
 
 extern "C" int naesat_cost_table_batch(int batch, const naesat_instance *insts, uint8_t *d_costs, uint64_t *n_sol,

@@ -99,12 +99,21 @@ __device__ __forceinline__ void rounds_down(typename G::V *v, typename G::V *til
     mask_butterflies<G, UA, P::R0::LO, P::R0::MASK>(v, active, A, B);
 }
 
+// Halved state (low pass): tile element u with bit T-1 set is the mirror
+// 2^(n-1) - 1 - x of the element x = u with that bit clear; its data and cost
+// bytes land in reverse memory order at position 2^T - 1 - (u mod 2^(T-1)).
+template <int T>
+__host__ __device__ __forceinline__ constexpr uint32_t land(uint32_t u) {
+    return (u >> (T - 1)) ? ((1u << T) - 1u - (u & ((1u << (T - 1)) - 1u))) : u;
+}
+
 // Stores the tile (thread pointer + r * stride), fusing the p_succ / norm
 // partials and the adjoint seed P psi when this is the evolution's last pass.
-// sc: the tile's cost bytes in shared memory, indexed by tile element.
-template <typename R, int LO>
+// sc: the tile's cost bytes in shared memory, indexed by tile element (by
+// landing position when Z2).
+template <typename R, int LO, bool Z2>
 __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename Cx<R>::V *sp, const uint8_t *sc,
-                                           typename Cx<R>::V *sa, uint64_t stride, bool reduce, double acc[2]) {
+                                           typename Cx<R>::V *sa, int64_t stride, bool reduce, double acc[2]) {
     using V = typename Cx<R>::V;
     constexpr int NR = Cx<R>::NR;
     // Opaque to the compiler: otherwise it keeps the load phase's 32 offsets
@@ -119,7 +128,8 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
         for (int r = 0; r < NR; ++r) {
             const R w = v[r].x * v[r].x + v[r].y * v[r].y;
             nm += w;
-            const bool sol = sc[tile_elem<Cx<R>, LO>(tid, r)] == 0;
+            const uint32_t u = tile_elem<Cx<R>, LO>(tid, r);
+            const bool sol = sc[Z2 ? land<Cx<R>::T>(u) : u] == 0;
             if (sol) ps += w;
             if (sa) {
                 V z;
@@ -179,7 +189,42 @@ __device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const ui
     }
 }
 
-template <typename R, bool LOW, int MODE, bool UA1, bool UA2>
+// Halved state, low pass: the tile is the half-tile [base, base + H) and its
+// mirror block [mbase, mbase + H), H = 2^(T-1), each copied in memory order
+// (the mirror block lands at positions [H, 2H)).
+template <typename R>
+__device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const uint8_t *cs, uint64_t base,
+                                              uint64_t mbase, bool state, bool cost, typename Cx<R>::V *buf,
+                                              uint8_t *sc) {
+    using V = typename Cx<R>::V;
+    constexpr int T = Cx<R>::T;
+    constexpr int EPC = 16 / (int)sizeof(V);
+    constexpr int NT = Cx<R>::PT;
+    constexpr int NCH = (1 << T) / EPC / NT;
+    constexpr int CCH = (1 << T) / 16 / NT;
+    constexpr uint32_t HC = (1u << (T - 1)) / 16;  // cost chunks per half
+    const uint32_t tid = threadIdx.x;
+    if (state) {
+        char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
+        const V *reg = st + base + EPC * tid;
+        const V *mir = st + mbase + EPC * tid;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const V *src = j < NCH / 2 ? reg + (size_t)EPC * NT * j : mir + (size_t)EPC * NT * (j - NCH / 2);
+            cp_async16(dst + (size_t)16 * NT * j, src);
+        }
+    }
+    if (cost) {
+#pragma unroll
+        for (int j = 0; j < CCH; ++j) {
+            const uint32_t q = tid + NT * j;
+            const uint8_t *src = q < HC ? cs + base + 16 * q : cs + mbase + 16 * (q - HC);
+            cp_async16(sc + 16 * q, src);
+        }
+    }
+}
+
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
                                            typename Cx<R>::V *tile, uint8_t *scs) {
     using G = Cx<R>;
@@ -197,28 +242,39 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     // Stores go straight from registers: thread pointer + r * stride (the plan
     // keeps the row width at 4 bits in high passes and both store mappings put
     // the registers above bit 4, so register bits are strided).
+    static_assert(!Z2 || (LOW && MODE != MODE_FUSED), "the halved state changes the low pass only");
     const uint64_t ld_t = elem_offset(tile_elem<G, LD>(tid, 0), a.row, a.lo);
     const uint64_t ld_s = LOW ? (1ull << LD) : (1ull << (a.lo + LD - a.row));
     const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
-    const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
+    const int64_t st_s = LOW ? (1ll << LC) : (1ll << (a.lo + LC - a.row));
+    // halved state: the mirror of element x of the stored half is M - x
+    const uint64_t M = (1ull << a.n) - 1;
+    constexpr uint32_t H = 1u << (T - 1);
+    const uint32_t z_u0 = tile_elem<G, LC>(tid, 0);  // its bit T - 1 is a thread bit in every store mapping
+    const bool z_mir = Z2 && (z_u0 >> (T - 1));
+    auto base_of = [&](uint64_t tt) { return Z2 ? (tt << (T - 1)) : tile_base(tt, a.row, a.lo, T); };
+    auto issue = [&](uint64_t tt, uint8_t *scb) {
+        const uint64_t bb = base_of(tt);
+        if (Z2)
+            issue_tile_z2<R>(st, cs, bb, M - bb - (H - 1), need_s, need_c, tile, scb);
+        else
+            issue_tile<R, LOW>(st, cs, bb, a.row, a.lo, need_s, need_c, tile, scb);
+    };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     uint64_t t = blockIdx.x;
-    if (t < a.tiles)
-        issue_tile<R, LOW>(st, cs, tile_base(t, a.row, a.lo, T), a.row, a.lo, need_s, need_c, tile, scs);
+    if (t < a.tiles) issue(t, scs);
     cp_async_commit();
     for (int i = 0; t < a.tiles; ++i, t += gridDim.x) {
         const int b = i & 1;
         uint8_t *sc = scs + ((size_t)b << T);
-        const uint64_t base = tile_base(t, a.row, a.lo, T);
+        const uint64_t base = base_of(t);
         const uint64_t tn = t + gridDim.x;
         // Once the tile's last exchange is read out the buffer is free: copy the
         // next tile into it (and its cost bytes into the other cost buffer)
         // while this tile finishes its last round and its stores.
         auto prefetch = [&]() {
             __syncthreads();
-            if (tn < a.tiles)
-                issue_tile<R, LOW>(st, cs, tile_base(tn, a.row, a.lo, T), a.row, a.lo, need_s, need_c, tile,
-                                   scs + ((size_t)(b ^ 1) << T));
+            if (tn < a.tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
             cp_async_commit();
         };
         cp_async_wait_all();  // this tile's copies are done
@@ -226,7 +282,8 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         V v[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {  // load mapping on the dense buffer: consecutive lanes, no conflicts
-            const uint32_t u = tile_elem<G, LD>(tid, r);
+            const uint32_t u0 = tile_elem<G, LD>(tid, r);
+            const uint32_t u = Z2 ? land<T>(u0) : u0;
             if (MODE == MODE_INIT)
                 v[r] = stab[sc[u]];
             else if (MODE == MODE_PHASE)
@@ -239,10 +296,18 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
             rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2, prefetch);
-            store_tile<R, LD>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, ld_s, a.reduce, acc);
+            store_tile<R, LD, false>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, (int64_t)ld_s,
+                                     a.reduce, acc);
         } else {
             rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1, prefetch);
-            store_tile<R, LC>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce, acc);
+            if (Z2) {  // the mirror half stores in descending order
+                const uint64_t ul0 = z_u0 & (H - 1);
+                V *sp = z_mir ? st + (M - base - ul0) : st + base + ul0;
+                store_tile<R, LC, true>(v, sp, sc, nullptr, z_mir ? -st_s : st_s, a.reduce, acc);
+            } else {
+                store_tile<R, LC, false>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce,
+                                         acc);
+            }
         }
     }
     if (a.reduce) {
@@ -266,7 +331,7 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
 // cost-byte buffers, then the phase table.
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
-template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT>
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT, bool Z2 = false>
 __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                             const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
@@ -283,7 +348,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constan
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2>(a, stab, tile, scs);
+    pass_tiles<R, LOW, MODE, UA1, UA2, Z2>(a, stab, tile, scs);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -494,11 +559,21 @@ struct PassKernels {
                           pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE>},
                          {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE>,
                           pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE>}};
+    // halved state: low-pass variants with the mirror qubit
+    KFull init_z2[2] = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, true>,
+                        pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, true>};
+    KFull phase_z2[2] = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE, true>,
+                         pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE, true>};
+    KNone plain_z2[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, true>,
+                         pass_kernel<R, true, MODE_PLAIN, true, false, 1, true>};
     cudaError_t init() {
         const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
         std::vector<const void *> ks;
         for (int i = 0; i < 2; ++i) {
             ks.push_back((const void *)phase_low[i]);
+            ks.push_back((const void *)init_z2[i]);
+            ks.push_back((const void *)phase_z2[i]);
+            ks.push_back((const void *)plain_z2[i]);
             for (int j = 0; j < 2; ++j) {
                 ks.push_back((const void *)init_k[i][j]);
                 ks.push_back((const void *)plain[i][j]);
@@ -563,8 +638,9 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
     PassKernels<R> *pk = nullptr;
     int rc = pass_kernels<R>(&pk);
     if (rc) return rc;
+    const bool z2 = (r.flags & QAOA_Z2_HALF) != 0;
     Plan pl;
-    rc = make_plan(r.n, r.dtype, &pl);
+    rc = make_plan(r.n, r.dtype, &pl, z2);
     if (rc) return rc;
     constexpr int T = Cx<R>::T;
     const int sign = (r.flags & QAOA_MIXER_RX2B) ? -1 : 1;
@@ -583,7 +659,7 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         a.state = reinterpret_cast<V *>(r.state);
         a.cost = r.cost;
         a.partials = d_partials;
-        a.n = r.n;
+        a.n = pl.state_bits;  // index bits of the stored state (and of the cost table)
         a.m = r.m;
         if (low) {  // the whole tile is one contiguous row
             a.row = T;
@@ -609,23 +685,24 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
             a.A2 = (R)k2.A;
             a.B2 = (R)k2.B;
         }
-        a.tiles = 1ull << (r.n - T);
+        a.tiles = 1ull << (pl.state_bits - T);
         const int kind = low ? K_PASS_LOW : K_PASS_HIGH;
         profile_before(kind, stream);
         const int u1 = a.ua1 ? 1 : 0, u2 = a.ua2 ? 1 : 0;
+        const bool zl = z2 && low;
         if (L.mode == MODE_INIT) {
             fill_table<R>(tab, r, 0, sign);
-            pk->init_k[low][u1]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            (zl ? pk->init_z2[u1] : pk->init_k[low][u1])<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
         } else if (L.mode == MODE_PHASE) {
             if (!low) return set_error(QAOA_ECUDA, "schedule: phase-at-load on a strided pass");
             fill_table<R>(tab, r, L.la, sign);
-            pk->phase_low[u1]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            (zl ? pk->phase_z2[u1] : pk->phase_low[u1])<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
         } else if (L.mode == MODE_FUSED) {
             if (low) return set_error(QAOA_ECUDA, "schedule: fused low pass");
             fill_table<R>(tab, r, L.la + 1, sign);
             pk->fused[u1][u2]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
         } else {
-            pk->plain[low][u1]<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            (zl ? pk->plain_z2[u1] : pk->plain[low][u1])<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
         }
         rc = profile_after(kind, stream);
         if (rc) return rc;
@@ -715,6 +792,11 @@ static int evolve_common(int batch, int n, const uint8_t *d_cost, int m, int p, 
                          void *adj, void *stream_) {
     int rc = validate_evolve(batch, n, d_cost, m, p, gamma, beta, dtype, d_state);
     if (rc) return rc;
+    const bool z2 = (flags & QAOA_Z2_HALF) != 0;
+    if (z2 && n <= small_n_limit(dtype))
+        return set_error(QAOA_ERANGE, "halved state needs n > %d (n=%d)", small_n_limit(dtype), n);
+    if (z2 && adj) return set_error(QAOA_EINVAL, "the gradient does not take the halved state");
+    const double scale = z2 ? 2.0 : 1.0;  // each stored amplitude stands for x and not x
     cudaStream_t stream = (cudaStream_t)stream_;
     const bool want = p_succ || norm;
     EvolveReq r{batch, n, m, p, dtype, flags, d_cost, d_state, adj, gamma, beta, nullptr};
@@ -739,7 +821,7 @@ static int evolve_common(int batch, int n, const uint8_t *d_cost, int m, int p, 
         return QAOA_OK;
     }
     if (n <= small_n_limit(dtype)) return set_error(QAOA_ERANGE, "n=%d too small for the pass path", n);
-    const int gx = pass_grid_x(dtype, n, batch);
+    const int gx = pass_grid_x(dtype, z2 ? n - 1 : n, batch);
     if (gx < 0) return QAOA_ECUDA;
     const size_t part = (size_t)batch * gx * 2 * sizeof(double);
     const size_t res = (size_t)batch * 2 * sizeof(double);
@@ -753,8 +835,8 @@ static int evolve_common(int batch, int n, const uint8_t *d_cost, int m, int p, 
     QAOA_CUDA_TRY(cudaMemcpyAsync(h, r.d_result, res, cudaMemcpyDeviceToHost, stream));
     QAOA_CUDA_TRY(cudaStreamSynchronize(stream));
     for (int b = 0; b < batch; ++b) {
-        if (p_succ) p_succ[b] = h[2 * b];
-        if (norm) norm[b] = h[2 * b + 1];
+        if (p_succ) p_succ[b] = scale * h[2 * b];
+        if (norm) norm[b] = scale * h[2 * b + 1];
     }
     return QAOA_OK;
 }

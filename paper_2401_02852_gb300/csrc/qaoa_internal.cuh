@@ -77,7 +77,9 @@ struct Pass {
 };
 struct Plan {
     int n = 0;
-    int tile_bits = 0;  // T
+    int state_bits = 0;  // index bits of the stored state (n, or n - 1 when halved)
+    int z2 = 0;          // halved by the global-flip symmetry
+    int tile_bits = 0;   // T
     int n_passes = 0;
     Pass pass[8];
 };
@@ -85,9 +87,9 @@ constexpr int T_C64 = 13;   // 2^13 complex64 = 64 KiB tile
 constexpr int T_C128 = 12;  // 2^12 complex128 = 64 KiB tile
 constexpr int G_MAX_C64 = 9;
 constexpr int G_MAX_C128 = 8;
-int make_plan(int n, int dtype, Plan *plan);
+int make_plan(int n, int dtype, Plan *plan, bool z2 = false);
 // Plan for a tile of 2^T amplitudes and high groups of at most gmax bits.
-int make_plan_geo(int n, int T, int gmax, Plan *plan);
+int make_plan_geo(int n, int T, int gmax, Plan *plan, bool z2 = false);
 
 // One launch of the forward evolution: pass `pass` of the plan for layer `la`.
 // Modes: 0 = first pass of layer 0 (the state |+> is generated from the phase
@@ -141,12 +143,12 @@ int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d
                             cudaStream_t stream);
 // One table with the clause records passed as kernel parameters (no staging).
 int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned long long *d_stats,
-                          cudaStream_t stream);
+                          cudaStream_t stream, bool half = false);
 
 // Multi-pass evolution of `batch` states (device side only, no host sync).
 // `tables` holds p layers x (m + 1) complex FP64 entries (interleaved).
 struct EvolveReq {
-    int batch, n, m, p, dtype, flags;
+    int batch, n, m, p, dtype, flags;  // flags & QAOA_Z2_HALF: halved state and half cost tables
     const uint8_t *cost;
     void *state;
     void *adj;          // nullable: if set, the last pass also writes P psi into it

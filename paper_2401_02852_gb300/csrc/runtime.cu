@@ -154,28 +154,36 @@ int profile_after(int kind, cudaStream_t stream) {
 }
 
 // ---------------------------------------------------------------------------
-int make_plan_geo(int n, int T, int G, Plan *plan) {
-    if (n < T + 1 || n > QAOA_MAX_N) return set_error(QAOA_ERANGE, "plan: n=%d outside [%d, %d]", n, T + 1, QAOA_MAX_N);
+int make_plan_geo(int n, int T, int G, Plan *plan, bool z2) {
+    // In the halved representation the stored state has n - 1 index bits and
+    // the low pass covers T - 1 of them plus the mirror (the top qubit).
+    const int nb = z2 ? n - 1 : n;
+    const int low = z2 ? T - 1 : T;
+    if (nb < T || n > QAOA_MAX_N || (!z2 && n < T + 1))
+        return set_error(QAOA_ERANGE, "plan: n=%d outside [%d, %d]", n, T + 1, QAOA_MAX_N);
     plan->n = n;
+    plan->state_bits = nb;
+    plan->z2 = z2 ? 1 : 0;
     plan->tile_bits = T;
     plan->pass[0] = {0, T, T};
     // High passes all span G bits with rows of T - G contiguous amplitudes; the
-    // last group ends at bit n, so it may re-cover already mixed bits, which it
+    // last group ends at bit nb, so it may re-cover already mixed bits, which it
     // carries without butterflies (`bits` counts only the new ones).
     int np = 0;
-    for (int lo = T; lo < n; lo += G) {
+    for (int lo = low; lo < nb; lo += G) {
         if (1 + np >= 8) return set_error(QAOA_ERANGE, "plan: n=%d needs too many passes", n);
-        const int glo = lo + G <= n ? lo : n - G;
-        plan->pass[1 + np] = {glo, lo + G <= n ? G : n - lo, T - G};
+        const int glo = lo + G <= nb ? lo : nb - G;
+        plan->pass[1 + np] = {glo, lo + G <= nb ? G : nb - lo, T - G};
         ++np;
     }
     plan->n_passes = 1 + np;
     return QAOA_OK;
 }
 
-int make_plan(int n, int dtype, Plan *plan) {
+int make_plan(int n, int dtype, Plan *plan, bool z2) {
     if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype %d", dtype);
-    return dtype == QAOA_C64 ? make_plan_geo(n, T_C64, G_MAX_C64, plan) : make_plan_geo(n, T_C128, G_MAX_C128, plan);
+    return dtype == QAOA_C64 ? make_plan_geo(n, T_C64, G_MAX_C64, plan, z2)
+                             : make_plan_geo(n, T_C128, G_MAX_C128, plan, z2);
 }
 
 std::vector<Launch> make_schedule(int n_passes, int p) {
@@ -253,9 +261,9 @@ int qaoa_version(void) { return 100; }
 
 int qaoa_release_scratch(void) { return release_all_scratch(); }
 
-int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits) {
+int qaoa_plan(int n, int dtype, int flags, int *group_lo, int *group_bits, int *row_bits) {
     Plan pl;
-    int rc = make_plan(n, dtype, &pl);
+    int rc = make_plan(n, dtype, &pl, (flags & QAOA_Z2_HALF) != 0);
     if (rc) return rc;
     for (int i = 0; i < pl.n_passes; ++i) {
         if (group_lo) group_lo[i] = pl.pass[i].lo;
@@ -265,10 +273,11 @@ int qaoa_plan(int n, int dtype, int *group_lo, int *group_bits, int *row_bits) {
     return pl.n_passes;
 }
 
-int qaoa_pass_schedule(int n, int p, int dtype, int max_launches, int *pass_index, int *layer, int *mode) {
+int qaoa_pass_schedule(int n, int p, int dtype, int flags, int max_launches, int *pass_index, int *layer,
+                       int *mode) {
     Plan pl;
     if (p < 0) return set_error(QAOA_EINVAL, "p=%d", p);
-    int rc = make_plan(n, dtype, &pl);
+    int rc = make_plan(n, dtype, &pl, (flags & QAOA_Z2_HALF) != 0);
     if (rc) return rc;
     const std::vector<Launch> seq = make_schedule(pl.n_passes, p);
     for (size_t i = 0; i < seq.size() && (int)i < max_launches; ++i) {

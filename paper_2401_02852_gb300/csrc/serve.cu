@@ -106,7 +106,9 @@ static int ensure_stage(Slot &s, size_t bytes) {
 // Launch one large request on slot s (stream ordered, no host sync).
 static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
     const int dtype = sv->o.dtype;
-    const size_t N = (size_t)1 << q.n;
+    // with QAOA_Z2_HALF the request keeps only the half state (global-flip symmetry)
+    const bool z2 = (sv->o.flags & QAOA_Z2_HALF) != 0;
+    const size_t N = (size_t)1 << (z2 ? q.n - 1 : q.n);
     int rc;
     naesat_instance inst{q.n, q.m, q.k, q.var.data(), q.neg.data()};
     // results layout in staging: [0..2) stats (u64), [2..4) p_succ, norm
@@ -116,8 +118,8 @@ static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
     unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(s.d_stage);
     double *d_res = reinterpret_cast<double *>(s.d_stage + 16);
     QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 16, s.stream));
-    if ((rc = launch_cost_table_one(&inst, (uint8_t *)s.d_cost, d_stats, s.stream))) return rc;
-    const int gx = pass_grid_x(dtype, q.n, 1);
+    if ((rc = launch_cost_table_one(&inst, (uint8_t *)s.d_cost, d_stats, s.stream, z2))) return rc;
+    const int gx = pass_grid_x(dtype, z2 ? q.n - 1 : q.n, 1);
     if (gx < 0) return QAOA_ECUDA;
     if (s.part_cap < (size_t)gx * 2) {
         if (s.d_part) cudaFree(s.d_part);
@@ -232,7 +234,8 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
 
 static size_t footprint(const qaoa_server *sv, int n, bool packed) {
     const size_t N = (size_t)1 << n;
-    return packed ? N : N * (1 + es_of(sv->o.dtype));
+    if (packed) return N;
+    return ((sv->o.flags & QAOA_Z2_HALF) ? N / 2 : N) * (1 + es_of(sv->o.dtype));
 }
 
 // Publishes the results of a finished slot (scheduler thread, lock held).
@@ -258,10 +261,11 @@ static void retire(qaoa_server *sv, Slot &s) {
         } else {
             const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s.h_stage);
             const double *res = reinterpret_cast<const double *>(s.h_stage + 16);
-            r.n_sol = st[0];
+            const double f = (sv->o.flags & QAOA_Z2_HALF) ? 2.0 : 1.0;  // halved state and table
+            r.n_sol = (uint64_t)(f * (double)st[0]);
             r.max_cost = (uint32_t)st[1];
-            r.p_succ = res[0];
-            r.norm = res[1];
+            r.p_succ = f * res[0];
+            r.norm = f * res[1];
         }
         r.status = r.max_cost > 255 ? QAOA_ERANGE : QAOA_OK;
         if (r.status) sv->counters[6]++;

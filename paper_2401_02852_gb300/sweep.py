@@ -51,27 +51,28 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
                     results[(n, p)] = json.load(f)
         if not todo:
             continue
-        per = (1 << n) * (1 + es)
+        # The halved state (exact: NAE's global-flip symmetry) halves memory and bytes.
+        per = (1 << (n - 1)) * (1 + es)
         chunk = int(max(1, min(seeds, mem_budget // per)))
         psucc = {p: [] for p in todo}
         nsol = []
         for c0 in range(0, seeds, chunk):
             B = min(chunk, seeds - c0)
-            costs = torch.empty((B, 1 << n), dtype=torch.uint8, device="cuda")
+            costs = torch.empty((B, 1 << (n - 1)), dtype=torch.uint8, device="cuda")
             insts = []
             for j in range(B):
                 def count(inst, j=j):
-                    return api.cost_table(inst, out=costs[j])[1]
+                    return api.cost_table_half(inst, out=costs[j])[1]
                 inst, s = gen.satisfiable_instance(f"sweep-k{k}", n, k, r, c0 + j, count)
                 insts.append(inst)
                 nsol.append(s)
             m = insts[0].m
-            states = torch.empty((B, 1 << n), dtype=api.TORCH_DTYPE[api.dtype_code(dtype)], device="cuda")
+            states = torch.empty((B, 1 << (n - 1)), dtype=api.TORCH_DTYPE[api.dtype_code(dtype)], device="cuda")
             for p in todo:
                 g, b = gen.linear_ramp(p)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                _, ps_b, _ = api.evolve_batch(n, costs, m, g, b, dtype, out=states)
+                _, ps_b, _ = api.evolve_batch(n, costs, m, g, b, dtype, flags=api.Z2_HALF, out=states)
                 t_gpu += time.perf_counter() - t0
                 amp_layers += B * (1 << n) * p
                 psucc[p].extend(float(x) for x in ps_b)

@@ -27,10 +27,10 @@ def _sync():
 
 
 def serve_workload(count: int = 20000, rate_hz: float = 200.0, n_range=(14, 26), p_range=(1, 20),
-                   n_streams: int = 4, seed: int = 0, baseline: bool = True) -> dict:
+                   n_streams: int = 4, seed: int = 0, baseline: bool = True, z2: bool = True) -> dict:
     reqs = gen.serving_requests(count, rate_hz=rate_hz, n_range=n_range, p_range=p_range, seed=seed)
     warm = gen.serving_requests(16, rate_hz=1e6, n_range=n_range, p_range=p_range, seed=seed + 1)
-    with serve.Server("c64", n_streams=n_streams) as s:
+    with serve.Server("c64", n_streams=n_streams, flags=api.Z2_HALF if z2 else 0) as s:
         for rq in warm:
             s.wait(s.submit(rq.instance, rq.gamma, rq.beta))
         res, wall = serve.replay(s, reqs)
@@ -38,6 +38,7 @@ def serve_workload(count: int = 20000, rate_hz: float = 200.0, n_range=(14, 26),
     lat = np.array([r.latency_s for r in res])
     amp_layers = sum((1 << rq.instance.n) * rq.p for rq in reqs)
     out = {"requests": count, "rate_hz": rate_hz, "n_range": list(n_range), "p_range": list(p_range),
+           "server_halved_state": z2,
            "server": serve.latency_summary(lat, wall, count) | {"amp_layer_per_s": amp_layers / wall},
            "server_stats": stats, "errors": int(sum(r.status != 0 for r in res))}
     if baseline:

@@ -48,11 +48,11 @@ def test_version_and_kernel_names(lib):
     assert "pass_low" in names and "cost_table" in names
 
 
-def _plan(lib, n, dtype):
+def _plan(lib, n, dtype, flags=0):
     lo = (ctypes.c_int * 8)()
     bits = (ctypes.c_int * 8)()
     row = (ctypes.c_int * 8)()
-    k = lib.qaoa_plan(n, dtype, lo, bits, row)
+    k = lib.qaoa_plan(n, dtype, flags, lo, bits, row)
     return k, [(lo[i], bits[i], row[i]) for i in range(max(k, 0))]
 
 
@@ -70,8 +70,8 @@ def test_plan_covers_every_qubit_once(lib, dtype, T, G):
 
 
 def test_plan_rejects_out_of_range(lib):
-    assert lib.qaoa_plan(50, 0, None, None, None) == _lib_code("ERANGE")
-    assert lib.qaoa_plan(20, 7, None, None, None) == _lib_code("EINVAL")
+    assert lib.qaoa_plan(50, 0, 0, None, None, None) == _lib_code("ERANGE")
+    assert lib.qaoa_plan(20, 7, 0, None, None, None) == _lib_code("EINVAL")
     assert b"dtype" in lib.qaoa_last_error()
 
 
@@ -98,31 +98,34 @@ def test_argument_validation_precedes_device_work(lib):
                          None, None, None, None) == _lib_code("EINVAL")
 
 
-def _schedule(lib, n, p, dtype):
+def _schedule(lib, n, p, dtype, flags=0):
     cap = 8 * p + 8
     idx, lay, mod = (ctypes.c_int * cap)(), (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
-    k = lib.qaoa_pass_schedule(n, p, dtype, cap, idx, lay, mod)
+    k = lib.qaoa_pass_schedule(n, p, dtype, flags, cap, idx, lay, mod)
     return [(idx[i], lay[i], mod[i]) for i in range(k)]
 
 
 @pytest.mark.parametrize("dtype,T", [(0, 13), (1, 12)])
 @pytest.mark.parametrize("p", [0, 1, 2, 5, 10])
-def test_schedule_applies_each_layer_in_order(lib, dtype, T, p):
+@pytest.mark.parametrize("z2", [False, True])
+def test_schedule_applies_each_layer_in_order(lib, dtype, T, p, z2):
     """Replays the launch sequence symbolically: every layer applies its phase
     once, then mixes every qubit exactly once, before the next layer's phase
-    (the layer product of the QAOA output state)."""
+    (the layer product of the QAOA output state).  In the halved plan the low
+    pass mixes qubits [0, T - 1) and the top qubit n - 1 (the mirror)."""
+    flags = 2 if z2 else 0
     for n in (T + 1, 22, 30, 32):
-        _, passes = _plan(lib, n, dtype)
+        _, passes = _plan(lib, n, dtype, flags)
         G = T - passes[1][2]
 
         def qubits(i):
             if i == 0:
-                return list(range(T))
+                return list(range(T - 1)) + [n - 1] if z2 else list(range(T))
             lo, bits, _ = passes[i]
             return list(range(lo + G - bits, lo + G))
 
         events = []
-        sched = _schedule(lib, n, p, dtype)
+        sched = _schedule(lib, n, p, dtype, flags)
         for pi, l, mode in sched:
             if mode in (0, 3):
                 events.append(("phase", l, None))

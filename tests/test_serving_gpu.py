@@ -104,3 +104,19 @@ def test_invalid_request_rejected_at_submit():
         with pytest.raises(QaoaError):
             s.submit(*_req(12, 1, 0)[:1], [float("nan")], [0.1])
         assert s.stats()["submitted"] == 0
+
+
+def test_halved_state_server_matches_full():
+    """With QAOA_Z2_HALF the unpacked requests run on the halved state: same
+    p_succ (complex64 tolerance), same solution counts, half the footprint."""
+    from paper_2401_02852_gb300._lib import Z2_HALF
+    reqs = [_req(n, p, 30 + n, tag="srv-z2") for n, p in ((15, 3), (18, 5), (21, 2), (24, 4))]
+    with Server("c64") as s:
+        full = [s.wait(s.submit(*r)) for r in reqs]
+    with Server("c64", flags=Z2_HALF) as s:
+        half = [s.wait(s.submit(*r)) for r in reqs]
+        peak = s.stats()["peak_bytes"]
+    for a, b in zip(full, half):
+        assert b.status == 0 and a.n_sol == b.n_sol and a.max_cost == b.max_cost
+        assert abs(a.p_succ - b.p_succ) <= 1e-5 * a.p_succ and abs(b.norm - 1) < 1e-5
+    assert peak <= (1 << 23) * 9  # the largest request's half table + half state
