@@ -104,8 +104,8 @@ def algorithmic_bytes(n: int, p: int, dtype: str):
     """Minimal HBM bytes each launch of the evolution must move, from the
     library's own launch schedule: every pass reads and writes the state once;
     the first pass of layer 0 only writes it (|+> comes from the phase table);
-    a pass that applies a phase reads the cost table once, and so does the last
-    pass (p_succ needs C).  Returns per-kind byte totals and launch counts."""
+    a pass that applies a phase (fused or phase-at-load) reads the cost table
+    once, and so does the last pass (p_succ needs C).  Returns per-kind byte totals and launch counts."""
     from paper_2401_02852_gb300 import api
 
     es = 8 if dtype == "c64" else 16
@@ -117,7 +117,7 @@ def algorithmic_bytes(n: int, p: int, dtype: str):
         if mode == 0:
             b = N * (es + 1)
         else:
-            b = N * 2 * es + (N if (mode == 2 or i + 1 == len(seq)) else 0)
+            b = N * 2 * es + (N if (mode in (2, 3) or i + 1 == len(seq)) else 0)
         out[kind] += b
         out["launches"][kind] += 1
     return out

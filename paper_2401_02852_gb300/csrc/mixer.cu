@@ -107,21 +107,31 @@ __host__ __device__ __forceinline__ constexpr uint32_t land(uint32_t u) {
     return (u >> (T - 1)) ? ((1u << T) - 1u - (u & ((1u << (T - 1)) - 1u))) : u;
 }
 
-// Stores the tile (thread pointer + r * stride), fusing the p_succ / norm
-// partials and the adjoint seed P psi when this is the evolution's last pass.
+// Stores the tile from mapping LO, fusing the p_succ / norm partials and the
+// adjoint seed P psi when this is the evolution's last pass.  sp: the thread's
+// first element; register r adds the state offset of tile element r << LO,
+// i.e. its row part plus its group part times gstride = 2^lo (ROW: the
+// tile's row bits).  In the halved state's mirror half (low pass) the offsets
+// run downwards.  Indices inside one instance fit in 32 bits (n <= 32).
 // sc: the tile's cost bytes in shared memory, indexed by tile element (by
 // landing position when Z2).
-template <typename R, int LO, bool Z2>
+template <typename R, int LO, int ROW, bool Z2, bool RED>
 __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename Cx<R>::V *sp, const uint8_t *sc,
-                                           typename Cx<R>::V *sa, int64_t stride, bool reduce, double acc[2]) {
+                                           typename Cx<R>::V *sa, uint32_t gstride, bool mirror, bool reduce,
+                                           double acc[2]) {
     using V = typename Cx<R>::V;
     constexpr int NR = Cx<R>::NR;
     // Opaque to the compiler: otherwise it keeps the load phase's 32 offsets
-    // r * stride live across the whole tile to reuse them here.
-    asm volatile("" : "+l"(sp), "+l"(stride));
+    // live across the whole tile to reuse them here.
+    asm volatile("" : "+l"(sp), "+r"(gstride));
+    auto off = [&](int r) -> int64_t {
+        const uint32_t u = (uint32_t)r << LO;
+        const uint32_t o = (u & ((1u << ROW) - 1u)) + (u >> ROW) * gstride;
+        return (Z2 && mirror) ? -(int64_t)o : (int64_t)o;
+    };
 #pragma unroll
-    for (int r = 0; r < NR; ++r) sp[r * stride] = v[r];
-    if (reduce) {
+    for (int r = 0; r < NR; ++r) sp[off(r)] = v[r];
+    if (RED && reduce) {
         R ps = 0, nm = 0;
         const uint32_t tid = threadIdx.x;
 #pragma unroll
@@ -135,7 +145,7 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
                 V z;
                 z.x = sol ? v[r].x : R(0);
                 z.y = sol ? v[r].y : R(0);
-                sa[r * stride] = z;
+                sa[off(r)] = z;
             }
         }
         acc[0] += (double)ps;
@@ -159,7 +169,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // buf[u]; thread tid takes chunks tid + PT j, whose addresses are a thread
 // base plus j times a stride.
 template <typename R, bool LOW>
-__device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const uint8_t *cs, uint64_t base, int row,
+__device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const uint8_t *cs, uint32_t base, int row,
                                            int lo, bool state, bool cost, typename Cx<R>::V *buf, uint8_t *sc) {
     using V = typename Cx<R>::V;
     constexpr int T = Cx<R>::T;
@@ -170,22 +180,19 @@ __device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const ui
     const uint32_t tid = threadIdx.x;
     if (state) {
         // chunk q = tid + PT j covers tile elements [EPC q, EPC q + EPC)
-        const uint64_t u0 = (uint64_t)EPC * tid;
-        const uint64_t off0 = elem_offset((uint32_t)u0, row, lo);
         // the bits of EPC * NT * j lie above those of EPC * tid and above the row
         // bits, so the offset is linear in j
-        const uint64_t step = elem_offset((uint32_t)(EPC * NT), row, lo);
-        const V *src = st + base + off0;
+        const uint32_t off0 = base + elem_offset32((uint32_t)EPC * tid, row, lo);
+        const uint32_t step = elem_offset32((uint32_t)(EPC * NT), row, lo);
         char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
 #pragma unroll
-        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * NT * j, src + step * j);
+        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * NT * j, st + (off0 + step * j));
     }
     if (cost) {
-        const uint64_t off0 = elem_offset(16u * tid, row, lo);
-        const uint64_t step = elem_offset(16u * NT, row, lo);
-        const uint8_t *src = cs + base + off0;
+        const uint32_t off0 = base + elem_offset32(16u * tid, row, lo);
+        const uint32_t step = elem_offset32(16u * NT, row, lo);
 #pragma unroll
-        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + NT * j), src + step * j);
+        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + NT * j), cs + (off0 + step * j));
     }
 }
 
@@ -193,8 +200,8 @@ __device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const ui
 // mirror block [mbase, mbase + H), H = 2^(T-1), each copied in memory order
 // (the mirror block lands at positions [H, 2H)).
 template <typename R>
-__device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const uint8_t *cs, uint64_t base,
-                                              uint64_t mbase, bool state, bool cost, typename Cx<R>::V *buf,
+__device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const uint8_t *cs, uint32_t base,
+                                              uint32_t mbase, bool state, bool cost, typename Cx<R>::V *buf,
                                               uint8_t *sc) {
     using V = typename Cx<R>::V;
     constexpr int T = Cx<R>::T;
@@ -224,7 +231,7 @@ __device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const
     }
 }
 
-template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2>
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2, bool RED, int HROW>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
                                            typename Cx<R>::V *tile, uint8_t *scs) {
     using G = Cx<R>;
@@ -237,44 +244,47 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     V *st = a.state + (inst << a.n);
     V *adj = a.adj ? a.adj + (inst << a.n) : nullptr;
     const uint8_t *cs = a.cost + (inst << a.n);
-    const bool need_c = MODE != MODE_PLAIN || a.reduce;
+    // Only the evolution's last pass reduces (a plain pass, or the initial one
+    // when p = 0); RED compiles that path in.
+    const bool red = RED && a.reduce;
+    const bool need_c = MODE != MODE_PLAIN || red;
+    constexpr int row = LOW ? T : HROW;  // contiguous tile bits
     const bool need_s = MODE != MODE_INIT;
-    // Stores go straight from registers: thread pointer + r * stride (the plan
-    // keeps the row width at 4 bits in high passes and both store mappings put
-    // the registers above bit 4, so register bits are strided).
+    // Stores go straight from registers: thread pointer + the register's offset.
     static_assert(!Z2 || (LOW && MODE != MODE_FUSED), "the halved state changes the low pass only");
-    const uint64_t ld_t = elem_offset(tile_elem<G, LD>(tid, 0), a.row, a.lo);
-    const uint64_t ld_s = LOW ? (1ull << LD) : (1ull << (a.lo + LD - a.row));
-    const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
-    const int64_t st_s = LOW ? (1ll << LC) : (1ll << (a.lo + LC - a.row));
+    // State indices of one instance fit in 32 bits (n <= 32).
+    const uint32_t ld_t = elem_offset32(tile_elem<G, LD>(tid, 0), row, a.lo);
+    const uint32_t st_t = elem_offset32(tile_elem<G, LC>(tid, 0), row, a.lo);
+    const uint32_t gstride = LOW ? 0u : (1u << a.lo);
     // halved state: the mirror of element x of the stored half is M - x
-    const uint64_t M = (1ull << a.n) - 1;
+    const uint32_t M = (uint32_t)((1ull << a.n) - 1);
     constexpr uint32_t H = 1u << (T - 1);
     const uint32_t z_u0 = tile_elem<G, LC>(tid, 0);  // its bit T - 1 is a thread bit in every store mapping
     const bool z_mir = Z2 && (z_u0 >> (T - 1));
-    auto base_of = [&](uint64_t tt) { return Z2 ? (tt << (T - 1)) : tile_base(tt, a.row, a.lo, T); };
-    auto issue = [&](uint64_t tt, uint8_t *scb) {
-        const uint64_t bb = base_of(tt);
+    auto base_of = [&](uint32_t tt) { return Z2 ? (tt << (T - 1)) : tile_base32(tt, row, a.lo, T); };
+    auto issue = [&](uint32_t tt, uint8_t *scb) {
+        const uint32_t bb = base_of(tt);
         if (Z2)
             issue_tile_z2<R>(st, cs, bb, M - bb - (H - 1), need_s, need_c, tile, scb);
         else
-            issue_tile<R, LOW>(st, cs, bb, a.row, a.lo, need_s, need_c, tile, scb);
+            issue_tile<R, LOW>(st, cs, bb, row, a.lo, need_s, need_c, tile, scb);
     };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
-    uint64_t t = blockIdx.x;
-    if (t < a.tiles) issue(t, scs);
+    const uint32_t tiles = (uint32_t)a.tiles;
+    uint32_t t = blockIdx.x;
+    if (t < tiles) issue(t, scs);
     cp_async_commit();
-    for (int i = 0; t < a.tiles; ++i, t += gridDim.x) {
+    for (int i = 0; t < tiles; ++i, t += gridDim.x) {
         const int b = i & 1;
         uint8_t *sc = scs + ((size_t)b << T);
-        const uint64_t base = base_of(t);
-        const uint64_t tn = t + gridDim.x;
+        const uint32_t base = base_of(t);
+        const uint32_t tn = t + gridDim.x;
         // Once the tile's last exchange is read out the buffer is free: copy the
         // next tile into it (and its cost bytes into the other cost buffer)
         // while this tile finishes its last round and its stores.
         auto prefetch = [&]() {
             __syncthreads();
-            if (tn < a.tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
+            if (tn < tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
             cp_async_commit();
         };
         cp_async_wait_all();  // this tile's copies are done
@@ -296,21 +306,20 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
             rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2, prefetch);
-            store_tile<R, LD, false>(v, st + base + ld_t, sc, adj ? adj + base + ld_t : nullptr, (int64_t)ld_s,
-                                     a.reduce, acc);
+            store_tile<R, LD, row, false, false>(v, st + (base + ld_t), sc, nullptr, gstride, false, false, acc);
         } else {
             rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1, prefetch);
             if (Z2) {  // the mirror half stores in descending order
-                const uint64_t ul0 = z_u0 & (H - 1);
-                V *sp = z_mir ? st + (M - base - ul0) : st + base + ul0;
-                store_tile<R, LC, true>(v, sp, sc, nullptr, z_mir ? -st_s : st_s, a.reduce, acc);
+                const uint32_t ul0 = z_u0 & (H - 1);
+                V *sp = z_mir ? st + (M - base - ul0) : st + (base + ul0);
+                store_tile<R, LC, row, true, RED>(v, sp, sc, nullptr, gstride, z_mir, red, acc);
             } else {
-                store_tile<R, LC, false>(v, st + base + st_t, sc, adj ? adj + base + st_t : nullptr, st_s, a.reduce,
-                                         acc);
+                store_tile<R, LC, row, false, RED>(v, st + (base + st_t), sc, adj ? adj + (base + st_t) : nullptr,
+                                                   gstride, false, red, acc);
             }
         }
     }
-    if (a.reduce) {
+    if (red) {
         block_sum<2, G::PT>(acc);
         if (threadIdx.x == 0) {
             double *out = a.partials + 2 * (inst * gridDim.x + blockIdx.x);
@@ -331,7 +340,8 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
 // cost-byte buffers, then the phase table.
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
-template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT, bool Z2 = false>
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT, bool Z2 = false, bool RED = false,
+          int HROW = HIGH_ROW>
 __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                             const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
@@ -348,7 +358,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constan
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2, Z2>(a, stab, tile, scs);
+    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW>(a, stab, tile, scs);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -544,28 +554,48 @@ struct PassKernels {
     using KFull = void (*)(PassArgs<R>, Full);
     using KNone = void (*)(PassArgs<R>, None);
     // [low][ua1] for init / plain, [ua1] for phase-at-load (low) and
-    // [ua1][ua2] for fused (high: the low pass never fuses)
+    // [ua1][ua2] for fused (high: the low pass never fuses).  Only the last pass
+    // reduces: a plain pass (plain_red), or the low initial pass when p = 0.
     KFull init_k[2][2] = {{pass_kernel<R, false, MODE_INIT, false, false, MAX_TABLE>,
                            pass_kernel<R, false, MODE_INIT, true, false, MAX_TABLE>},
-                          {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE>,
-                           pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE>}};
+                          {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, false, true>,
+                           pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, false, true>}};
     KFull phase_low[2] = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE>,
                           pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE>};
     KNone plain[2][2] = {{pass_kernel<R, false, MODE_PLAIN, false, false, 1>,
                           pass_kernel<R, false, MODE_PLAIN, true, false, 1>},
                          {pass_kernel<R, true, MODE_PLAIN, false, false, 1>,
                           pass_kernel<R, true, MODE_PLAIN, true, false, 1>}};
+    KNone plain_red[2][2] = {{pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, true>,
+                              pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, true>},
+                             {pass_kernel<R, true, MODE_PLAIN, false, false, 1, false, true>,
+                              pass_kernel<R, true, MODE_PLAIN, true, false, 1, false, true>}};
     KFull fused[2][2] = {{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE>,
                           pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE>},
                          {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE>,
                           pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE>}};
+    // high passes with rows of WROW bits (complex64: 32 amplitudes, 256 B);
+    // complex128 has no wide rows and these are the narrow kernels again
+    static constexpr int WROW = sizeof(R) == 4 ? HIGH_ROW + 1 : HIGH_ROW;
+    KFull init_w[2] = {pass_kernel<R, false, MODE_INIT, false, false, MAX_TABLE, false, false, WROW>,
+                       pass_kernel<R, false, MODE_INIT, true, false, MAX_TABLE, false, false, WROW>};
+    KNone plain_w[2] = {pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, false, WROW>,
+                        pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, false, WROW>};
+    KNone plain_red_w[2] = {pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, true, WROW>,
+                            pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, true, WROW>};
+    KFull fused_w[2][2] = {{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE, false, false, WROW>,
+                            pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE, false, false, WROW>},
+                           {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE, false, false, WROW>,
+                            pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE, false, false, WROW>}};
     // halved state: low-pass variants with the mirror qubit
-    KFull init_z2[2] = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, true>,
-                        pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, true>};
+    KFull init_z2[2] = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, true, true>,
+                        pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, true, true>};
     KFull phase_z2[2] = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE, true>,
                          pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE, true>};
     KNone plain_z2[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, true>,
                          pass_kernel<R, true, MODE_PLAIN, true, false, 1, true>};
+    KNone plain_z2_red[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, true, true>,
+                             pass_kernel<R, true, MODE_PLAIN, true, false, 1, true, true>};
     cudaError_t init() {
         const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
         std::vector<const void *> ks;
@@ -574,9 +604,15 @@ struct PassKernels {
             ks.push_back((const void *)init_z2[i]);
             ks.push_back((const void *)phase_z2[i]);
             ks.push_back((const void *)plain_z2[i]);
+            ks.push_back((const void *)plain_z2_red[i]);
+            ks.push_back((const void *)init_w[i]);
+            ks.push_back((const void *)plain_w[i]);
+            ks.push_back((const void *)plain_red_w[i]);
             for (int j = 0; j < 2; ++j) {
+                ks.push_back((const void *)fused_w[i][j]);
                 ks.push_back((const void *)init_k[i][j]);
                 ks.push_back((const void *)plain[i][j]);
+                ks.push_back((const void *)plain_red[i][j]);
                 ks.push_back((const void *)fused[i][j]);
             }
         }
@@ -666,12 +702,16 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
             a.lo = T;
             a.active = r.p > 0 ? ((1u << T) - 1u) : 0u;
         } else {
+            if (ps.row != HIGH_ROW && ps.row != PassKernels<R>::WROW)
+                return set_error(QAOA_ECUDA, "plan: high pass rows of %d bits", ps.row);
             a.row = ps.row;
             a.lo = ps.lo;
             a.active = ((1u << ps.bits) - 1u) << (T - ps.bits);
         }
         const bool last = i + 1 == seq.size();
         a.reduce = (last && (want || r.adj)) ? 1 : 0;
+        if (a.reduce && !(L.mode == MODE_PLAIN || (L.mode == MODE_INIT && low)))
+            return set_error(QAOA_ECUDA, "schedule: the last pass has mode %d", L.mode);
         a.adj = (last && r.adj) ? reinterpret_cast<V *>(r.adj) : nullptr;
         const LayerCoef k1 = r.p > 0 ? layer_coef(r.beta[L.la], sign) : LayerCoef{1.0, 1.0, 0.0, true};
         a.ua1 = k1.unit_a;
@@ -690,9 +730,12 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         profile_before(kind, stream);
         const int u1 = a.ua1 ? 1 : 0, u2 = a.ua2 ? 1 : 0;
         const bool zl = z2 && low;
+        const bool wide = !low && ps.row != HIGH_ROW;  // rows of WROW bits
         if (L.mode == MODE_INIT) {
             fill_table<R>(tab, r, 0, sign);
-            (zl ? pk->init_z2[u1] : pk->init_k[low][u1])<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            (zl ? pk->init_z2[u1] : wide ? pk->init_w[u1] : pk->init_k[low][u1])<<<grid, block,
+                                                                                 pass_smem<R>(true, r.m), stream>>>(
+                a, *tab);
         } else if (L.mode == MODE_PHASE) {
             if (!low) return set_error(QAOA_ECUDA, "schedule: phase-at-load on a strided pass");
             fill_table<R>(tab, r, L.la, sign);
@@ -700,9 +743,12 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         } else if (L.mode == MODE_FUSED) {
             if (low) return set_error(QAOA_ECUDA, "schedule: fused low pass");
             fill_table<R>(tab, r, L.la + 1, sign);
-            pk->fused[u1][u2]<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
+            (wide ? pk->fused_w[u1][u2] : pk->fused[u1][u2])<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a,
+                                                                                                              *tab);
         } else {
-            (zl ? pk->plain_z2[u1] : pk->plain[low][u1])<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            auto k = a.reduce ? (zl ? pk->plain_z2_red[u1] : wide ? pk->plain_red_w[u1] : pk->plain_red[low][u1])
+                              : (zl ? pk->plain_z2[u1] : wide ? pk->plain_w[u1] : pk->plain[low][u1]);
+            k<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
         }
         rc = profile_after(kind, stream);
         if (rc) return rc;

@@ -25,6 +25,8 @@
 namespace qaoa {
 
 constexpr int PT = 256;  // threads per pass CTA (8 thread bits)
+// Row width (bits) of every high-pass tile: 16 contiguous amplitudes.
+constexpr int HIGH_ROW = 4;
 
 // Tile geometry: element type R, 2^T amplitudes per tile, 2^RB per thread,
 // 2^(T - RB) threads.  The load mapping (LO = T - RB) puts the registers on the
@@ -119,12 +121,20 @@ __device__ __forceinline__ uint64_t elem_offset(uint32_t u, int row, int lo) {
     return (uint64_t)(u & ((1u << row) - 1u)) | ((uint64_t)(u >> row) << lo);
 }
 
+// The same in 32 bits (state indices of one instance, n <= 32).
+__device__ __forceinline__ uint32_t elem_offset32(uint32_t u, int row, int lo) {
+    return (u & ((1u << row) - 1u)) | ((u >> row) << lo);
+}
+
 // State index of the first element of tile t: the tile id fills the free bits
 // [row, lo) and [lo + G, n), G = T - row.
 __device__ __forceinline__ uint64_t tile_base(uint64_t t, int row, int lo, int T) {
     const int G = T - row;
     const int span = lo - row;
     return ((t & ((1ull << span) - 1ull)) << row) | ((t >> span) << (lo + G));
+}
+__device__ __forceinline__ uint32_t tile_base32(uint32_t t, int row, int lo, int T) {
+    return (uint32_t)tile_base(t, row, lo, T);
 }
 
 template <typename V>

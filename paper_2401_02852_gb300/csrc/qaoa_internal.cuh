@@ -89,7 +89,10 @@ constexpr int G_MAX_C64 = 9;
 constexpr int G_MAX_C128 = 8;
 int make_plan(int n, int dtype, Plan *plan, bool z2 = false);
 // Plan for a tile of 2^T amplitudes and high groups of at most gmax bits.
-int make_plan_geo(int n, int T, int gmax, Plan *plan, bool z2 = false);
+// With `wide`, groups that can spare a bit take gmax - 1 bits and rows of
+// T - gmax + 1 bits instead (twice the contiguous bytes per row, which the
+// HBM streams more efficiently at large strides); the top groups go wide first.
+int make_plan_geo(int n, int T, int gmax, Plan *plan, bool z2 = false, bool wide = false);
 
 // One launch of the forward evolution: pass `pass` of the plan for layer `la`.
 // Modes: 0 = first pass of layer 0 (the state |+> is generated from the phase

@@ -2,6 +2,7 @@
 // pass planning and the FP64 per-layer coefficients.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -154,7 +155,7 @@ int profile_after(int kind, cudaStream_t stream) {
 }
 
 // ---------------------------------------------------------------------------
-int make_plan_geo(int n, int T, int G, Plan *plan, bool z2) {
+int make_plan_geo(int n, int T, int G, Plan *plan, bool z2, bool wide) {
     // In the halved representation the stored state has n - 1 index bits and
     // the low pass covers T - 1 of them plus the mirror (the top qubit).
     const int nb = z2 ? n - 1 : n;
@@ -166,23 +167,32 @@ int make_plan_geo(int n, int T, int G, Plan *plan, bool z2) {
     plan->z2 = z2 ? 1 : 0;
     plan->tile_bits = T;
     plan->pass[0] = {0, T, T};
-    // High passes all span G bits with rows of T - G contiguous amplitudes; the
-    // last group ends at bit nb, so it may re-cover already mixed bits, which it
-    // carries without butterflies (`bits` counts only the new ones).
-    int np = 0;
-    for (int lo = low; lo < nb; lo += G) {
-        if (1 + np >= 8) return set_error(QAOA_ERANGE, "plan: n=%d needs too many passes", n);
-        const int glo = lo + G <= nb ? lo : nb - G;
-        plan->pass[1 + np] = {glo, lo + G <= nb ? G : nb - lo, T - G};
-        ++np;
+    // k high groups cover the R bits above the low pass: narrow groups span G
+    // bits with rows of T - G contiguous amplitudes, wide ones G - 1 bits with
+    // rows of T - G + 1; as many groups go wide (top first) as the k G - R spare
+    // bits allow.  The last group ends at bit nb, so when the groups have room
+    // to spare it re-covers already mixed bits, which it carries without
+    // butterflies (`bits` counts only the new ones).
+    const int R = nb - low;
+    const int k = R > 0 ? (R + G - 1) / G : 0;
+    if (1 + k > 8) return set_error(QAOA_ERANGE, "plan: n=%d needs too many passes", n);
+    const int w = wide ? std::min(k, k * G - R) : 0;
+    int lo = low;
+    for (int i = 0; i < k; ++i) {
+        const int g = i >= k - w ? G - 1 : G;
+        const int glo = lo + g <= nb ? lo : nb - g;
+        plan->pass[1 + i] = {glo, lo + g <= nb ? g : nb - lo, T - g};
+        lo += g;
     }
-    plan->n_passes = 1 + np;
+    plan->n_passes = 1 + k;
     return QAOA_OK;
 }
 
 int make_plan(int n, int dtype, Plan *plan, bool z2) {
     if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype %d", dtype);
-    return dtype == QAOA_C64 ? make_plan_geo(n, T_C64, G_MAX_C64, plan, z2)
+    // complex64 rows of 16 amplitudes are 128 B: take wide groups (256 B rows)
+    // where the bit count allows; complex128 rows are 256 B already.
+    return dtype == QAOA_C64 ? make_plan_geo(n, T_C64, G_MAX_C64, plan, z2, true)
                              : make_plan_geo(n, T_C128, G_MAX_C128, plan, z2);
 }
 

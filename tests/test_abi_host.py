@@ -56,17 +56,24 @@ def _plan(lib, n, dtype, flags=0):
     return k, [(lo[i], bits[i], row[i]) for i in range(max(k, 0))]
 
 
-@pytest.mark.parametrize("dtype,T,G", [(0, 13, 9), (1, 12, 8)])
-def test_plan_covers_every_qubit_once(lib, dtype, T, G):
+@pytest.mark.parametrize("dtype,T,G,rows", [(0, 13, 9, (4, 5)), (1, 12, 8, (4,))])
+def test_plan_covers_every_qubit_once(lib, dtype, T, G, rows):
+    """Every qubit is mixed by exactly one pass; high groups span T - row bits
+    (complex64 also takes 256-byte rows of 5 bits, groups of 8), with no more
+    passes than groups of the widest size need."""
     for n in range(T + 1, 33):
         k, passes = _plan(lib, n, dtype)
         assert k == len(passes) >= 2
+        assert k - 1 == -(-(n - T) // G)
         mixed = list(range(passes[0][1]))
         assert passes[0] == (0, T, T)
         for lo, bits, row in passes[1:]:
-            assert row == T - G and lo >= row and lo + G <= n
-            mixed += list(range(lo + G - bits, lo + G))  # the top `bits` of the group
+            g = T - row
+            assert row in rows and lo >= row and lo + g <= n and 1 <= bits <= g
+            mixed += list(range(lo + g - bits, lo + g))  # the top `bits` of the group
         assert sorted(mixed) == list(range(n)), (n, passes)
+    if dtype == 0:  # n = 30: rows of 16 for bits 13..21, of 32 for bits 22..29
+        assert _plan(lib, 30, dtype)[1] == [(0, 13, 13), (13, 9, 4), (22, 8, 5)]
 
 
 def test_plan_rejects_out_of_range(lib):
@@ -116,13 +123,13 @@ def test_schedule_applies_each_layer_in_order(lib, dtype, T, p, z2):
     flags = 2 if z2 else 0
     for n in (T + 1, 22, 30, 32):
         _, passes = _plan(lib, n, dtype, flags)
-        G = T - passes[1][2]
 
         def qubits(i):
             if i == 0:
                 return list(range(T - 1)) + [n - 1] if z2 else list(range(T))
-            lo, bits, _ = passes[i]
-            return list(range(lo + G - bits, lo + G))
+            lo, bits, row = passes[i]
+            g = T - row
+            return list(range(lo + g - bits, lo + g))
 
         events = []
         sched = _schedule(lib, n, p, dtype, flags)
