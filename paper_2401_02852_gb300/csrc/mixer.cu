@@ -231,7 +231,7 @@ __device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const
     }
 }
 
-template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2, bool RED, int HROW>
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2, bool RED, int HROW, bool FULL>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
                                            typename Cx<R>::V *tile, uint8_t *scs) {
     using G = Cx<R>;
@@ -249,6 +249,11 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     const bool red = RED && a.reduce;
     const bool need_c = MODE != MODE_PLAIN || red;
     constexpr int row = LOW ? T : HROW;  // contiguous tile bits
+    // FULL: every group bit of the tile is butterflied (a compile-time mask, so
+    // the stages are straight-line code); otherwise the pass's runtime mask
+    // (a last group that re-covers mixed bits, or no butterflies when p = 0).
+    constexpr uint32_t full_mask = ((1u << T) - 1u) & ~(LOW ? 0u : (1u << row) - 1u);
+    const uint32_t active = FULL ? full_mask : a.active;
     const bool need_s = MODE != MODE_INIT;
     // Stores go straight from registers: thread pointer + the register's offset.
     static_assert(!Z2 || (LOW && MODE != MODE_FUSED), "the halved state changes the low pass only");
@@ -302,13 +307,13 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
                 v[r] = tile[u];
         }
         if (MODE == MODE_FUSED) {
-            rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1, NoHook());
+            rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, NoHook());
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
-            rounds_down<G, LOW, UA2>(v, tile, a.active, a.A2, a.B2, prefetch);
+            rounds_down<G, LOW, UA2>(v, tile, active, a.A2, a.B2, prefetch);
             store_tile<R, LD, row, false, false>(v, st + (base + ld_t), sc, nullptr, gstride, false, false, acc);
         } else {
-            rounds_up<G, LOW, UA1>(v, tile, a.active, a.A1, a.B1, prefetch);
+            rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, prefetch);
             if (Z2) {  // the mirror half stores in descending order
                 const uint32_t ul0 = z_u0 & (H - 1);
                 V *sp = z_mir ? st + (M - base - ul0) : st + (base + ul0);
@@ -341,7 +346,7 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT, bool Z2 = false, bool RED = false,
-          int HROW = HIGH_ROW>
+          int HROW = HIGH_ROW, bool FULL = true>
 __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
                                                             const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constan
         }
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW>(a, stab, tile, scs);
+    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW, FULL>(a, stab, tile, scs);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -547,76 +552,84 @@ static size_t pass_smem(bool phase, int m) {
            (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
+using KPtr = const void *;
+
+// The kernels of one kind of high pass: rows of HROW bits; FULL: every group
+// bit is butterflied.  [ua1] for init / plain, [ua1][ua2] for fused.
+template <typename R, int HROW, bool FULL>
+struct HighSet {
+    using Full = PhaseTab<R, MAX_TABLE>;
+    using None = PhaseTab<R, 1>;
+    void (*init[2])(PassArgs<R>, Full) = {pass_kernel<R, false, MODE_INIT, false, false, MAX_TABLE, false, false, HROW, FULL>,
+                                          pass_kernel<R, false, MODE_INIT, true, false, MAX_TABLE, false, false, HROW, FULL>};
+    void (*plain[2])(PassArgs<R>, None) = {pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, false, HROW, FULL>,
+                                           pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, false, HROW, FULL>};
+    void (*plain_red[2])(PassArgs<R>, None) = {pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, true, HROW, FULL>,
+                                               pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, true, HROW, FULL>};
+    void (*fused[2][2])(PassArgs<R>, Full) = {
+        {pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE, false, false, HROW, FULL>,
+         pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE, false, false, HROW, FULL>},
+        {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE, false, false, HROW, FULL>,
+         pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE, false, false, HROW, FULL>}};
+    void all(std::vector<KPtr> &ks) const {
+        for (int i = 0; i < 2; ++i) {
+            ks.push_back((KPtr)init[i]);
+            ks.push_back((KPtr)plain[i]);
+            ks.push_back((KPtr)plain_red[i]);
+            for (int j = 0; j < 2; ++j) ks.push_back((KPtr)fused[i][j]);
+        }
+    }
+};
+
+// The kernels of the low pass (Z2: the halved state's mirror variant); all
+// butterfly every tile bit, except init0 (p = 0: the initial state alone).
+template <typename R, bool Z2>
+struct LowSet {
+    using Full = PhaseTab<R, MAX_TABLE>;
+    using None = PhaseTab<R, 1>;
+    void (*init[2])(PassArgs<R>, Full) = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, Z2, true>,
+                                          pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, Z2, true>};
+    void (*init0)(PassArgs<R>, Full) = pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, Z2, true, HIGH_ROW, false>;
+    void (*phase[2])(PassArgs<R>, Full) = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE, Z2>,
+                                           pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE, Z2>};
+    void (*plain[2])(PassArgs<R>, None) = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, Z2>,
+                                           pass_kernel<R, true, MODE_PLAIN, true, false, 1, Z2>};
+    void (*plain_red[2])(PassArgs<R>, None) = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, Z2, true>,
+                                               pass_kernel<R, true, MODE_PLAIN, true, false, 1, Z2, true>};
+    void all(std::vector<KPtr> &ks) const {
+        ks.push_back((KPtr)init0);
+        for (int i = 0; i < 2; ++i) {
+            ks.push_back((KPtr)init[i]);
+            ks.push_back((KPtr)phase[i]);
+            ks.push_back((KPtr)plain[i]);
+            ks.push_back((KPtr)plain_red[i]);
+        }
+    }
+};
+
 template <typename R>
 struct PassKernels {
     using Full = PhaseTab<R, MAX_TABLE>;
     using None = PhaseTab<R, 1>;
-    using KFull = void (*)(PassArgs<R>, Full);
-    using KNone = void (*)(PassArgs<R>, None);
-    // [low][ua1] for init / plain, [ua1] for phase-at-load (low) and
-    // [ua1][ua2] for fused (high: the low pass never fuses).  Only the last pass
-    // reduces: a plain pass (plain_red), or the low initial pass when p = 0.
-    KFull init_k[2][2] = {{pass_kernel<R, false, MODE_INIT, false, false, MAX_TABLE>,
-                           pass_kernel<R, false, MODE_INIT, true, false, MAX_TABLE>},
-                          {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, false, true>,
-                           pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, false, true>}};
-    KFull phase_low[2] = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE>,
-                          pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE>};
-    KNone plain[2][2] = {{pass_kernel<R, false, MODE_PLAIN, false, false, 1>,
-                          pass_kernel<R, false, MODE_PLAIN, true, false, 1>},
-                         {pass_kernel<R, true, MODE_PLAIN, false, false, 1>,
-                          pass_kernel<R, true, MODE_PLAIN, true, false, 1>}};
-    KNone plain_red[2][2] = {{pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, true>,
-                              pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, true>},
-                             {pass_kernel<R, true, MODE_PLAIN, false, false, 1, false, true>,
-                              pass_kernel<R, true, MODE_PLAIN, true, false, 1, false, true>}};
-    KFull fused[2][2] = {{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE>,
-                          pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE>},
-                         {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE>,
-                          pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE>}};
     // high passes with rows of WROW bits (complex64: 32 amplitudes, 256 B);
-    // complex128 has no wide rows and these are the narrow kernels again
+    // complex128 has no wide rows and those are the narrow kernels again
     static constexpr int WROW = sizeof(R) == 4 ? HIGH_ROW + 1 : HIGH_ROW;
-    KFull init_w[2] = {pass_kernel<R, false, MODE_INIT, false, false, MAX_TABLE, false, false, WROW>,
-                       pass_kernel<R, false, MODE_INIT, true, false, MAX_TABLE, false, false, WROW>};
-    KNone plain_w[2] = {pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, false, WROW>,
-                        pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, false, WROW>};
-    KNone plain_red_w[2] = {pass_kernel<R, false, MODE_PLAIN, false, false, 1, false, true, WROW>,
-                            pass_kernel<R, false, MODE_PLAIN, true, false, 1, false, true, WROW>};
-    KFull fused_w[2][2] = {{pass_kernel<R, false, MODE_FUSED, false, false, MAX_TABLE, false, false, WROW>,
-                            pass_kernel<R, false, MODE_FUSED, false, true, MAX_TABLE, false, false, WROW>},
-                           {pass_kernel<R, false, MODE_FUSED, true, false, MAX_TABLE, false, false, WROW>,
-                            pass_kernel<R, false, MODE_FUSED, true, true, MAX_TABLE, false, false, WROW>}};
-    // halved state: low-pass variants with the mirror qubit
-    KFull init_z2[2] = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, true, true>,
-                        pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, true, true>};
-    KFull phase_z2[2] = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE, true>,
-                         pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE, true>};
-    KNone plain_z2[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, true>,
-                         pass_kernel<R, true, MODE_PLAIN, true, false, 1, true>};
-    KNone plain_z2_red[2] = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, true, true>,
-                             pass_kernel<R, true, MODE_PLAIN, true, false, 1, true, true>};
+    LowSet<R, false> low;
+    LowSet<R, true> low_z2;
+    HighSet<R, HIGH_ROW, true> high;     // [wide][full] below
+    HighSet<R, HIGH_ROW, false> high_part;
+    HighSet<R, WROW, true> wide;
+    HighSet<R, WROW, false> wide_part;
     cudaError_t init() {
         const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
-        std::vector<const void *> ks;
-        for (int i = 0; i < 2; ++i) {
-            ks.push_back((const void *)phase_low[i]);
-            ks.push_back((const void *)init_z2[i]);
-            ks.push_back((const void *)phase_z2[i]);
-            ks.push_back((const void *)plain_z2[i]);
-            ks.push_back((const void *)plain_z2_red[i]);
-            ks.push_back((const void *)init_w[i]);
-            ks.push_back((const void *)plain_w[i]);
-            ks.push_back((const void *)plain_red_w[i]);
-            for (int j = 0; j < 2; ++j) {
-                ks.push_back((const void *)fused_w[i][j]);
-                ks.push_back((const void *)init_k[i][j]);
-                ks.push_back((const void *)plain[i][j]);
-                ks.push_back((const void *)plain_red[i][j]);
-                ks.push_back((const void *)fused[i][j]);
-            }
-        }
-        for (const void *k : ks) {
+        std::vector<KPtr> ks;
+        low.all(ks);
+        low_z2.all(ks);
+        high.all(ks);
+        high_part.all(ks);
+        wide.all(ks);
+        wide_part.all(ks);
+        for (KPtr k : ks) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
             if (e != cudaSuccess) return e;
         }
@@ -729,26 +742,48 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         const int kind = low ? K_PASS_LOW : K_PASS_HIGH;
         profile_before(kind, stream);
         const int u1 = a.ua1 ? 1 : 0, u2 = a.ua2 ? 1 : 0;
-        const bool zl = z2 && low;
-        const bool wide = !low && ps.row != HIGH_ROW;  // rows of WROW bits
-        if (L.mode == MODE_INIT) {
-            fill_table<R>(tab, r, 0, sign);
-            (zl ? pk->init_z2[u1] : wide ? pk->init_w[u1] : pk->init_k[low][u1])<<<grid, block,
-                                                                                 pass_smem<R>(true, r.m), stream>>>(
-                a, *tab);
-        } else if (L.mode == MODE_PHASE) {
-            if (!low) return set_error(QAOA_ECUDA, "schedule: phase-at-load on a strided pass");
-            fill_table<R>(tab, r, L.la, sign);
-            (zl ? pk->phase_z2[u1] : pk->phase_low[u1])<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a, *tab);
-        } else if (L.mode == MODE_FUSED) {
-            if (low) return set_error(QAOA_ECUDA, "schedule: fused low pass");
-            fill_table<R>(tab, r, L.la + 1, sign);
-            (wide ? pk->fused_w[u1][u2] : pk->fused[u1][u2])<<<grid, block, pass_smem<R>(true, r.m), stream>>>(a,
-                                                                                                              *tab);
+        const size_t smem_phase = pass_smem<R>(true, r.m), smem_plain = pass_smem<R>(false, 0);
+        if (low) {
+            const LowSet<R, false> &ls = pk->low;
+            const LowSet<R, true> &lz = pk->low_z2;
+            if (L.mode == MODE_INIT) {
+                fill_table<R>(tab, r, 0, sign);
+                auto k = r.p == 0 ? (z2 ? lz.init0 : ls.init0) : (z2 ? lz.init[u1] : ls.init[u1]);
+                k<<<grid, block, smem_phase, stream>>>(a, *tab);
+            } else if (L.mode == MODE_PHASE) {
+                fill_table<R>(tab, r, L.la, sign);
+                (z2 ? lz.phase[u1] : ls.phase[u1])<<<grid, block, smem_phase, stream>>>(a, *tab);
+            } else if (L.mode == MODE_PLAIN) {
+                auto k = a.reduce ? (z2 ? lz.plain_red[u1] : ls.plain_red[u1]) : (z2 ? lz.plain[u1] : ls.plain[u1]);
+                k<<<grid, block, smem_plain, stream>>>(a, none);
+            } else {
+                return set_error(QAOA_ECUDA, "schedule: fused low pass");
+            }
         } else {
-            auto k = a.reduce ? (zl ? pk->plain_z2_red[u1] : wide ? pk->plain_red_w[u1] : pk->plain_red[low][u1])
-                              : (zl ? pk->plain_z2[u1] : wide ? pk->plain_w[u1] : pk->plain[low][u1]);
-            k<<<grid, block, pass_smem<R>(false, 0), stream>>>(a, none);
+            // rows of HIGH_ROW or WROW bits; FULL kernels when no bit of the group is a carried one
+            const bool wide = ps.row != HIGH_ROW, full = ps.bits == T - ps.row;
+            const HighSet<R, HIGH_ROW, true> &hn = pk->high;
+            const HighSet<R, HIGH_ROW, false> &hp = pk->high_part;
+            const HighSet<R, PassKernels<R>::WROW, true> &wn = pk->wide;
+            const HighSet<R, PassKernels<R>::WROW, false> &wp = pk->wide_part;
+            if (L.mode == MODE_INIT) {
+                fill_table<R>(tab, r, 0, sign);
+                auto k = wide ? (full ? wn.init[u1] : wp.init[u1]) : (full ? hn.init[u1] : hp.init[u1]);
+                k<<<grid, block, smem_phase, stream>>>(a, *tab);
+            } else if (L.mode == MODE_FUSED) {
+                fill_table<R>(tab, r, L.la + 1, sign);
+                auto k = wide ? (full ? wn.fused[u1][u2] : wp.fused[u1][u2])
+                              : (full ? hn.fused[u1][u2] : hp.fused[u1][u2]);
+                k<<<grid, block, smem_phase, stream>>>(a, *tab);
+            } else if (L.mode == MODE_PLAIN) {
+                auto k = a.reduce ? (wide ? (full ? wn.plain_red[u1] : wp.plain_red[u1])
+                                          : (full ? hn.plain_red[u1] : hp.plain_red[u1]))
+                                  : (wide ? (full ? wn.plain[u1] : wp.plain[u1])
+                                          : (full ? hn.plain[u1] : hp.plain[u1]));
+                k<<<grid, block, smem_plain, stream>>>(a, none);
+            } else {
+                return set_error(QAOA_ECUDA, "schedule: phase-at-load on a strided pass");
+            }
         }
         rc = profile_after(kind, stream);
         if (rc) return rc;
