@@ -17,6 +17,14 @@
 // sit in shared memory (one broadcast 16-byte load per clause) and each thread
 // counts two words per record load.  The number of
 // solutions (count 0) and the largest count come out of the same pass.
+//
+// Clause filtering.  A block takes 512 consecutive words at a time, so the
+// variables >= 14 (SUB_BITS) are constant over them.  A clause whose literals
+// on those variables are neither all true nor all false is violated nowhere in
+// the block; the block first keeps only the others, each reduced to its
+// variables 5..13 and to the one or two patterns still possible (for random
+// 5-literal clauses over 30 variables about 40% survive), then counts against
+// that list.  Counts are sums of 0/1 terms, so the list order is immaterial.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -172,21 +180,63 @@ __device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t plan
     }
 }
 
-// One table: each thread takes the word pair (X, X + half) over a grid-stride
-// loop, so every clause record loaded from shared memory serves 64 assignments.
-__device__ __forceinline__ void cost_table_body(int n, int m16, const uint4 *srec, uint8_t *cost,
-                                                unsigned long long *stats) {
+constexpr int SUB_WORDS = 2 * CT_THREADS;  // words per block step
+constexpr int SUB_BITS = 14;                // log2(32 SUB_WORDS): variables >= 14 are constant over a step
+
+// Keeps the clauses of srec[0, m) that can be violated somewhere in the words
+// [base, base + SUB_WORDS), reduced to variables 5..13, in alive[0, *count),
+// zero-padded to a multiple of 16.  Called by all threads of the block.
+__device__ __forceinline__ int filter_clauses(uint32_t base, int m, const uint4 *srec, uint4 *alive, int *count) {
+    constexpr uint32_t MID = (1u << SUB_BITS) - 32u;  // variables 5..13
+    const uint32_t xu = base << 5;                     // x bits >= 14 of the step (bits < 14 are zero)
+    if (threadIdx.x == 0) *count = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < m; i0 += CT_THREADS) {
+        const int i = i0 + threadIdx.x;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        bool keep = false;
+        if (i < m) {
+            r = srec[i];
+            const uint32_t umask = r.x & ~MID & ~31u;
+            const uint32_t tu = (xu ^ r.y) & umask;
+            const bool at = tu == umask, af = tu == 0u;  // uniform literals all true / all false
+            keep = at || af;
+            r = make_uint4(r.x & MID, r.y & MID, at ? r.z : 0u, af ? r.w : 0u);
+        }
+        const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, keep);
+        int pos = 0;
+        if (lane == 0 && ballot) pos = atomicAdd(count, __popc(ballot));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + __popc(ballot & ((1u << lane) - 1u));
+        if (keep) alive[pos] = r;
+    }
+    __syncthreads();
+    const int c = *count, c16 = (c + 15) & ~15;
+    for (int i = c + threadIdx.x; i < c16; i += CT_THREADS) alive[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    return c16;
+}
+
+// One table: each block steps through SUB_WORDS consecutive words at a time;
+// thread t takes words base + t and base + CT_THREADS + t, so every clause
+// record loaded from shared memory serves 64 assignments.
+__device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *srec, uint4 *alive, int *acount,
+                                                uint8_t *cost, unsigned long long *stats) {
     const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
-    const uint64_t half = (words + 1) / 2;
+    const uint64_t steps = (words + SUB_WORDS - 1) / SUB_WORDS;
     unsigned long long nsol = 0;
     uint32_t mx = 0;
-    for (uint64_t X = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; X < half;
-         X += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t X1 = X + half;
-        uint32_t p0[10], p1[10];
-        count_words2((uint32_t)X, (uint32_t)(X1 < words ? X1 : X), m16, srec, p0, p1);
-        emit_word(n, X, p0, cost, nsol, mx);
-        if (X1 < words) emit_word(n, X1, p1, cost, nsol, mx);
+    for (uint64_t sb = blockIdx.x; sb < steps; sb += gridDim.x) {
+        const uint32_t base = (uint32_t)(sb * SUB_WORDS);
+        const int c16 = filter_clauses(base, m, srec, alive, acount);
+        const uint64_t X0 = base + threadIdx.x, X1 = X0 + CT_THREADS;
+        if (X0 < words) {
+            uint32_t p0[10], p1[10];
+            count_words2((uint32_t)X0, (uint32_t)(X1 < words ? X1 : X0), c16, alive, p0, p1);
+            emit_word(n, X0, p0, cost, nsol, mx);
+            if (X1 < words) emit_word(n, X1, p1, cost, nsol, mx);
+        }
+        __syncthreads();  // the list is rebuilt for the next step
     }
     // warp then block reduction, one atomic pair per block
 #pragma unroll
@@ -219,13 +269,14 @@ constexpr int MAX_M16 = (QAOA_MAX_M + 15) / 16 * 16;
 __global__ void __launch_bounds__(CT_THREADS) cost_table_kernel(const __grid_constant__ CostParams prm, uint8_t *cost,
                                                                 unsigned long long *stats) {
     __shared__ uint4 srec[MAX_M16];
-    const int m16 = (prm.m + 15) / 16 * 16;
-    for (int i = threadIdx.x; i < m16; i += CT_THREADS) {
-        const ClauseRec r = i < prm.m ? prm.rec[i] : ClauseRec{0, 0, 0, 0};
+    __shared__ uint4 alive[MAX_M16];
+    __shared__ int acount;
+    for (int i = threadIdx.x; i < prm.m; i += CT_THREADS) {
+        const ClauseRec r = prm.rec[i];
         srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
     }
     __syncthreads();
-    cost_table_body(prm.n, m16, srec, cost, stats);
+    cost_table_body(prm.n, prm.m, srec, alive, &acount, cost, stats);
 }
 
 // Batched tables.  With ns == nullptr every instance has n qubits and its table
@@ -236,18 +287,19 @@ __global__ void __launch_bounds__(CT_THREADS) cost_table_batch_kernel(int n, con
                                                                       int m_stride, uint8_t *costs,
                                                                       unsigned long long *stats) {
     __shared__ uint4 srec[MAX_M16];
+    __shared__ uint4 alive[MAX_M16];
+    __shared__ int acount;
     const int inst = blockIdx.y;
     const int m = ms[inst];
-    const int m16 = (m + 15) / 16 * 16;
     const ClauseRec *g = recs + (size_t)inst * m_stride;
-    for (int i = threadIdx.x; i < m16; i += CT_THREADS) {
-        const ClauseRec r = i < m ? g[i] : ClauseRec{0, 0, 0, 0};
+    for (int i = threadIdx.x; i < m; i += CT_THREADS) {
+        const ClauseRec r = g[i];
         srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
     }
     __syncthreads();
     const int ni = ns ? ns[inst] : n;
     uint8_t *dst = ns ? costs + offs[inst] : costs + ((size_t)inst << n);
-    cost_table_body(ni, m16, srec, dst, stats + 2 * inst);
+    cost_table_body(ni, m, srec, alive, &acount, dst, stats + 2 * inst);
 }
 
 // ---------------------------------------------------------------------------
