@@ -15,6 +15,7 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -121,6 +122,32 @@ def algorithmic_bytes(n: int, p: int, dtype: str):
         out[kind] += b
         out["launches"][kind] += 1
     return out
+
+
+def profiled_traffic(kind: str, n: int, p: int, dtype: str):
+    """DRAM bytes per launch of `kind` (dram__bytes_read.sum + dram__bytes_write.sum,
+    averaged over one step's launches of that kind) from the committed ncu summary
+    profiles/traffic_n{n}_p{p}_{dtype}.txt, provided the kernel sources it names
+    still hash to the value recorded with the capture; otherwise None."""
+    path = os.path.join(ROOT, "profiles", f"traffic_n{n}_p{p}_{dtype}.txt")
+    try:
+        with open(path) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None, None
+    for ln in lines:
+        parts = ln.split()
+        if not parts or parts[0].startswith("#") or parts[0] != kind:
+            continue
+        fields = dict(x.split("=", 1) for x in parts[2:])
+        h = hashlib.sha256()
+        for name in fields["sources"].split(","):
+            with open(os.path.join(ROOT, "paper_2401_02852_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != fields["sources_sha256"]:
+            return None, "stale: the kernel sources changed after the capture"
+        return int(parts[1]), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def measured_peak():
@@ -258,8 +285,9 @@ def run_native(args, ws, rank, local):
         per_launch_bytes = alg[dom] / alg["launches"][dom]
         avg_ms = kinds[dom][1] / kinds[dom][0]
         achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
+        traffic, traffic_src = profiled_traffic(dom, n, p, dtype)
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms}
     # all pass kernels together, and the 1-pass floor (17 B per amp-layer for complex64)
     pass_ms = sum(kinds.get(k, (0, 0.0))[1] for k in ("pass_low", "pass_high")) / args.steps

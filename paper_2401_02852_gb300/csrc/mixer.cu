@@ -276,14 +276,26 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     const uint32_t tiles = (uint32_t)a.tiles;
-    uint32_t t = blockIdx.x;
+    // High passes that read both the state and the cost bytes take tiles in
+    // groups of GT = 64 B / (cost bytes per row): tiles GT q .. GT q + GT - 1,
+    // q = blockIdx.x + k gridDim.x.  Their rows are neighbours in memory, so the
+    // cost bytes of GT rows (one 64-byte DRAM burst) are fetched once and the
+    // group's later tiles find them in L2.  (The initial pass reads no state
+    // and keeps the plain order, in which concurrent tiles write neighbouring
+    // rows.)
+    constexpr uint32_t GT = (LOW || MODE == MODE_INIT) ? 1u : (row >= 6 ? 1u : 64u >> row);
+    const bool grouped = GT > 1 && tiles % GT == 0;
+    auto tile_at = [&](uint32_t i) -> uint32_t {
+        return grouped ? GT * (blockIdx.x + (i / GT) * gridDim.x) + (i % GT) : blockIdx.x + i * gridDim.x;
+    };
+    uint32_t t = tile_at(0);
     if (t < tiles) issue(t, scs);
     cp_async_commit();
-    for (int i = 0; t < tiles; ++i, t += gridDim.x) {
+    for (uint32_t i = 0; t < tiles; ++i, t = tile_at(i)) {
         const int b = i & 1;
         uint8_t *sc = scs + ((size_t)b << T);
         const uint32_t base = base_of(t);
-        const uint32_t tn = t + gridDim.x;
+        const uint32_t tn = tile_at(i + 1);
         // Once the tile's last exchange is read out the buffer is free: copy the
         // next tile into it (and its cost bytes into the other cost buffer)
         // while this tile finishes its last round and its stores.
