@@ -12,5 +12,7 @@ from .oracle import (  # noqa: F401
     evolve,
     grad,
     library_path,
+    running_time,
+    sample,
     success_prob,
 )

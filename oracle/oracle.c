@@ -230,3 +230,59 @@ int oracle_grad(int n, const uint16_t *cost, int p, const double *gamma, const d
     free(lam);
     return OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Bitstrings drawn from the output state (Sec. "Running Times": measuring the
+ * final state yields x with probability |Psi(x)|^2, and the running time of an
+ * instance is the number of such draws up to and including the first one that
+ * satisfies it).  The caller supplies one uniform u_j in [0, 1) per draw, so
+ * two implementations given the same uniforms make the same draws.  Draw j is
+ * the inverse of the cumulative distribution in index order:
+ *   F(x) = sum_{y <= x} |psi(y)|^2,   x_j = min { x : F(x) > u_j F(2^n - 1) },
+ * which never returns an x of probability zero. */
+int oracle_sample(int n, const double *psi_in, int k, const double *u, uint64_t *x_out) {
+    if (n < 1 || n > 30 || k < 0) return EINVAL_;
+    const double complex *psi = (const double complex *)psi_in;
+    const int64_t N = (int64_t)1 << n;
+    double *F = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!F) return ENOMEM_;
+    double run = 0.0;
+    for (int64_t x = 0; x < N; ++x) {
+        run += creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
+        F[x] = run;
+    }
+    for (int j = 0; j < k; ++j) {
+        const double t = u[j] * F[N - 1];
+        int64_t lo = 0, hi = N - 1; /* smallest x with F[x] > t (N - 1 if none) */
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (F[mid] > t)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        x_out[j] = (uint64_t)lo;
+    }
+    free(F);
+    return OK;
+}
+
+/* Running time of one instance over the given draws: 1 + the index of the
+ * first draw with C(x_j) = 0, or 0 when none of the k draws satisfies. */
+int oracle_running_time(int n, const uint16_t *cost, const double *psi_in, int k, const double *u,
+                        int64_t *running_time) {
+    if (k < 0) return EINVAL_;
+    uint64_t *xs = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(k > 0 ? k : 1));
+    if (!xs) return ENOMEM_;
+    int rc = oracle_sample(n, psi_in, k, u, xs);
+    if (rc == OK) {
+        *running_time = 0;
+        for (int j = 0; j < k; ++j)
+            if (cost[xs[j]] == 0) {
+                *running_time = j + 1;
+                break;
+            }
+    }
+    free(xs);
+    return rc;
+}

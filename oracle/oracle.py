@@ -51,6 +51,8 @@ def _load():
             lib.oracle_evolve.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int, P]
             lib.oracle_success_prob.argtypes = [ctypes.c_int, P, P, P, P]
             lib.oracle_grad.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int, P, P, P]
+            lib.oracle_sample.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P]
+            lib.oracle_running_time.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P]
             _lib = lib
     return _lib
 
@@ -142,3 +144,26 @@ def grad(n: int, cost, gamma, beta, sign: int = 1):
     if rc != 0:
         raise ValueError(f"oracle_grad failed ({rc})")
     return ps.value, dg, db
+
+
+def sample(n: int, psi, u) -> np.ndarray:
+    """Draws x_j = min{x : F(x) > u_j F_total} from |psi|^2 (inverse CDF in index order); uint64 [k]."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    xs = np.empty(u.shape[0], dtype=np.uint64)
+    rc = _load().oracle_sample(n, _ptr(psi), u.shape[0], _ptr(u), _ptr(xs))
+    if rc != 0:
+        raise ValueError(f"oracle_sample failed ({rc})")
+    return xs
+
+
+def running_time(n: int, cost, psi, u) -> int:
+    """1 + index of the first draw that satisfies the instance (C = 0), 0 if none does."""
+    cost = np.ascontiguousarray(cost, dtype=np.uint16)
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    rt = ctypes.c_int64()
+    rc = _load().oracle_running_time(n, _ptr(cost), _ptr(psi), u.shape[0], _ptr(u), ctypes.byref(rt))
+    if rc != 0:
+        raise ValueError(f"oracle_running_time failed ({rc})")
+    return rt.value

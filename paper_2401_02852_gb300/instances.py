@@ -101,6 +101,22 @@ def linear_ramp(p: int, scale: float = 0.8):
     return gamma, beta
 
 
+def random_state(tag: str, n: int, index: int = 0, sparsity: float = 0.0) -> np.ndarray:
+    """A seeded synthetic state: complex128 [2^n], re and im standard normal,
+    normalised; with `sparsity` > 0 that fraction of the amplitudes is zero.
+    (Random numbers only: an input for tests of the samplers.)"""
+    rng = rng_for(tag, n, index)
+    z = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    if sparsity > 0:
+        z[rng.random(1 << n) < sparsity] = 0
+    return z / np.sqrt(np.sum(np.abs(z) ** 2))
+
+
+def uniforms(tag: str, count: int, index: int = 0) -> np.ndarray:
+    """`count` seeded uniforms in [0, 1) (the draws of a sampler)."""
+    return rng_for(tag, count, index).random(count)
+
+
 def poisson_arrivals(rate_hz: float, count: int, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
     rng = rng_for("arrivals", seed, int(rate_hz * 1000), count)
