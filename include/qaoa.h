@@ -172,6 +172,38 @@ int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_state, int dty
 int qaoa_success_prob_noalloc(int n, const uint8_t *d_cost, const void *d_state, int dtype, double *p_succ,
                               double *norm, void *stream);
 
+/* ---- sampling and running times ------------------------------------------------
+ * Bitstrings measured from a state (Sec. "Running Times": a measurement of the
+ * output state yields x with probability |Psi(x)|^2, and the running time of an
+ * instance is the number of measured bitstrings up to and including the first
+ * that satisfies it).  The caller supplies the randomness: one uniform u_j in
+ * [0, 1) per draw, device float64 [k] (per instance [batch][k]).  Draw j is
+ *   x_j = min { x : F(x) > u_j F_total },   F(x) = sum_{y <= x} |psi(y)|^2
+ * (inverse CDF in index order; probabilities formed in FP64, per-block sums,
+ * so it differs from a sequential FP64 scan only for u_j within rounding of a
+ * step of F).  An x of probability zero is never drawn; a u_j outside [0, 1)
+ * yields the first or the last x of nonzero probability; a state of norm zero
+ * draws 0.  With QAOA_Z2_HALF the state and table are the halved ones (the x
+ * with bit n-1 clear) and draws cover all 2^n assignments.  k in [1, 2^30].
+ *
+ * qaoa_sample: d_x device uint64 [k], written.  Asynchronous on the stream.
+ */
+int qaoa_sample(int n, const void *d_state, int dtype, int flags, int k, const double *d_u, uint64_t *d_x,
+                void *stream);
+
+/* Running time over the draws of d_u: *running_time = 1 + the index of the
+ * first draw with C(x_j) = 0, or 0 when none of the k draws satisfies (draw
+ * again with fresh uniforms and add k).  d_x: device uint64 [k] receiving the
+ * draws, nullable (library scratch).  Synchronises the stream. */
+int qaoa_running_time(int n, const uint8_t *d_cost, const void *d_state, int dtype, int flags, int k,
+                      const double *d_u, int64_t *running_time, uint64_t *d_x, void *stream);
+
+/* Batched running times for `batch` instances of one n: d_costs [batch][2^n]
+ * (halved: [batch][2^(n-1)]), d_states likewise, d_u [batch][k],
+ * running_time host int64 [batch].  batch in [1, 65535].  Synchronises. */
+int qaoa_running_time_batch(int batch, int n, const uint8_t *d_costs, const void *d_states, int dtype, int flags,
+                            int k, const double *d_u, int64_t *running_time, void *stream);
+
 /* ---- gradient ----------------------------------------------------------------
  * dp_succ/dgamma_l and dp_succ/dbeta_l by a reverse sweep that recomputes the
  * states backward with inverse layers (no stored intermediate states).  The

@@ -59,6 +59,9 @@ SIGNATURES = {
     "qaoa_evolve_batch": (I, [I, I, P, I, I, P, P, I, I, P, P, P, P]),
     "qaoa_success_prob": (I, [I, P, P, I, P, P, P]),
     "qaoa_success_prob_noalloc": (I, [I, P, P, I, P, P, P]),
+    "qaoa_sample": (I, [I, P, I, I, I, P, P, P]),
+    "qaoa_running_time": (I, [I, P, P, I, I, I, P, P, P, P]),
+    "qaoa_running_time_batch": (I, [I, I, P, P, I, I, I, P, P, P]),
     "qaoa_grad": (I, [I, P, I, I, P, P, I, I, P, P, P, P, P, P]),
     "qaoa_grad_batch": (I, [I, I, P, I, I, P, P, I, I, P, P, P, P, P, P]),
     "qaoa_server_create": (I, [P, P]),

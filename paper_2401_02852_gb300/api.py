@@ -145,6 +145,48 @@ def success_prob(n: int, cost: torch.Tensor, state: torch.Tensor, stream=None):
     return ps.value, nm.value
 
 
+def _uniforms(u, count: int) -> torch.Tensor:
+    u = torch.as_tensor(u, dtype=torch.float64)
+    u = u.to("cuda").contiguous()
+    if u.numel() != count:
+        raise ValueError(f"expected {count} uniforms, got {u.numel()}")
+    return u
+
+
+def sample(n: int, state: torch.Tensor, u, flags: int = 0, out: Optional[torch.Tensor] = None, stream=None):
+    """Bitstrings drawn from |state|^2 by inverse CDF, one per uniform in `u`
+    (Sec. "Running Times"); int64 device tensor [k] (x < 2^n)."""
+    k = int(np.prod(np.shape(u)))
+    du = _uniforms(u, k)
+    if out is None:
+        out = torch.empty(k, dtype=torch.int64, device="cuda")
+    check(load().qaoa_sample(n, _ptr(state), dtype_code(state.dtype), flags, k, _ptr(du), _ptr(out),
+                             _stream(stream)))
+    return out
+
+
+def running_time(n: int, cost: torch.Tensor, state: torch.Tensor, u, flags: int = 0, stream=None) -> int:
+    """1 + index of the first draw (one per uniform) that satisfies the
+    instance, or 0 when none does."""
+    k = int(np.prod(np.shape(u)))
+    du = _uniforms(u, k)
+    rt = ctypes.c_int64()
+    check(load().qaoa_running_time(n, _ptr(cost), _ptr(state), dtype_code(state.dtype), flags, k, _ptr(du),
+                                   ctypes.byref(rt), None, _stream(stream)))
+    return rt.value
+
+
+def running_time_batch(n: int, costs: torch.Tensor, states: torch.Tensor, u, flags: int = 0, stream=None):
+    """Running times of a batch (same n): u has shape [batch, k]; int64 numpy [batch]."""
+    batch = states.shape[0]
+    k = int(np.prod(np.shape(u))) // batch
+    du = _uniforms(u, batch * k)
+    rt = np.zeros(batch, dtype=np.int64)
+    check(load().qaoa_running_time_batch(batch, n, _ptr(costs), _ptr(states), dtype_code(states.dtype), flags, k,
+                                         _ptr(du), _np_ptr(rt), _stream(stream)))
+    return rt
+
+
 def grad(n: int, cost: torch.Tensor, m: int, gamma, beta, dtype="c64", flags: int = MIXER_PAPER,
          work: Optional[tuple] = None, stream=None):
     """(p_succ, dp/dgamma [p], dp/dbeta [p]) by the recompute-backward adjoint sweep."""

@@ -58,6 +58,7 @@ enum KernelKind {
     K_ADJ_HIGH,
     K_ADJ_SEED,
     K_SERVE_SMALL,
+    K_SAMPLE,
     K_NUM_KINDS
 };
 // Call before / after a launch on `stream`.  `after` checks the launch status.

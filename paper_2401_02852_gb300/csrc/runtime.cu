@@ -119,7 +119,7 @@ static thread_local cudaEvent_t t_pending = nullptr;
 
 static const char *k_names[K_NUM_KINDS] = {
     "cost_table", "pass_low", "pass_high", "small_n", "reduce",
-    "success_prob", "adjoint_low", "adjoint_high", "adjoint_seed", "serve_small"};
+    "success_prob", "adjoint_low", "adjoint_high", "adjoint_seed", "serve_small", "sample"};
 
 static cudaEvent_t take_event() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
