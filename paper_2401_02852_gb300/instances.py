@@ -117,6 +117,17 @@ def uniforms(tag: str, count: int, index: int = 0) -> np.ndarray:
     return rng_for(tag, count, index).random(count)
 
 
+def device_uniforms(tag: str, shape, index: int = 0, device: str = "cuda"):
+    """Seeded uniforms in [0, 1) made on the device (torch Philox generator
+    seeded from this module's stream), float64 tensor of `shape`."""
+    import torch
+
+    seed = int(rng_for(tag, *(int(d) for d in shape), index).integers(0, 2 ** 62))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return torch.rand(tuple(shape), dtype=torch.float64, device=device, generator=g)
+
+
 def poisson_arrivals(rate_hz: float, count: int, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
     rng = rng_for("arrivals", seed, int(rate_hz * 1000), count)

@@ -4,7 +4,10 @@ For each n, `seeds` satisfiable CNF(n, k, r) instances (rejection sampling,
 satisfiability decided by the bit-exact cost table), each evaluated at every
 depth in `ps` with the linear-ramp angles.  Per (n, p) the median of 1/p_succ
 is fitted as 2^(c n + d) (Sec. "Running Times": exponents are fitted to a
-power law of the form 2^(c n + d), in bits).  Results are written one file per
+power law of the form 2^(c n + d), in bits).  With `running_times`, each
+instance's running time (bitstrings drawn from its output state until one
+satisfies it, Sec. "Running Times") is sampled on the GPU, and the median over
+instances is reported beside 1 / E[p_succ].  Results are written one file per
 (n, p) and skipped when present, so an interrupted sweep resumes.
 """
 from __future__ import annotations
@@ -37,12 +40,45 @@ def fit_exponent(ns: Iterable[int], values: Iterable[float]):
     return float(c), float(d)
 
 
+def sample_running_times(n: int, costs, states, flags: int, tag: str, first_k: int = 1024,
+                         max_draws: int = 1 << 26, draw_budget: int = 1 << 27):
+    """Running time of every instance of a batch: rounds of k draws (k growing
+    4x per round) for the instances still without a satisfying draw; an
+    instance still unresolved after `max_draws` draws is censored (-1)."""
+    B = states.shape[0]
+    rt = np.zeros(B, dtype=np.int64)
+    done = np.zeros(B, dtype=np.int64)  # draws taken so far
+    open_ = np.arange(B)
+    k, rnd = first_k, 0
+    while open_.size and k <= max_draws:
+        step = max(1, draw_budget // k)
+        for c0 in range(0, open_.size, step):
+            idx = open_[c0:c0 + step]
+            u = gen.device_uniforms(tag, (idx.size, k), rnd * 1_000_003 + int(idx[0]))
+            if idx.size == B:  # every instance: no gather
+                cs, st = costs, states
+            else:
+                sel = torch.as_tensor(idx, device=states.device)
+                cs, st = costs.index_select(0, sel), states.index_select(0, sel)
+            got = api.running_time_batch(n, cs, st, u, flags=flags)
+            hit = got > 0
+            rt[idx[hit]] = done[idx[hit]] + got[hit]
+            done[idx] += k
+        open_ = open_[rt[open_] == 0]
+        k *= 4
+        rnd += 1
+    rt[open_] = -1
+    return rt
+
+
 def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int = 5, r: float = 8.0,
-              dtype: str = "c64", out_dir: Optional[str] = None, mem_budget: int = 48 << 30, log=print):
+              dtype: str = "c64", out_dir: Optional[str] = None, mem_budget: int = 48 << 30, log=print,
+              running_times: bool = False):
     es = 8 if dtype == "c64" else 16
     results = {}
     amp_layers = 0
     t_gpu = 0.0
+    t_rt = 0.0
     for n in ns:
         todo = [p for p in ps if not (out_dir and os.path.exists(os.path.join(out_dir, f"n{n}_p{p}.json")))]
         for p in ps:
@@ -55,6 +91,7 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
         per = (1 << (n - 1)) * (1 + es)
         chunk = int(max(1, min(seeds, mem_budget // per)))
         psucc = {p: [] for p in todo}
+        rts = {p: [] for p in todo}
         nsol = []
         for c0 in range(0, seeds, chunk):
             B = min(chunk, seeds - c0)
@@ -76,6 +113,11 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
                 t_gpu += time.perf_counter() - t0
                 amp_layers += B * (1 << n) * p
                 psucc[p].extend(float(x) for x in ps_b)
+                if running_times:
+                    t1 = time.perf_counter()
+                    rts[p].extend(int(x) for x in sample_running_times(
+                        n, costs, states, api.Z2_HALF, f"rt-n{n}-p{p}-c{c0}"))
+                    t_rt += time.perf_counter() - t1
             del states, costs
             torch.cuda.empty_cache()
         for p in todo:
@@ -83,6 +125,12 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
             rec = {"n": n, "p": p, "k": k, "r": r, "seeds": seeds, "median_inv_psucc": float(np.median(1.0 / arr)),
                    "mean_psucc": float(arr.mean()), "mean_nsol_frac": float(np.mean(nsol) / 2 ** n),
                    "psucc": psucc[p]}
+            if running_times:
+                rt = np.array(rts[p])
+                # censored instances (-1) count as longer than any observed time
+                rt_med = np.median(np.where(rt < 0, np.iinfo(np.int64).max, rt))
+                rec.update({"median_running_time": float(rt_med), "inv_mean_psucc": float(1.0 / arr.mean()),
+                            "censored_running_times": int(np.sum(rt < 0)), "running_times": rts[p]})
             results[(n, p)] = rec
             if out_dir:
                 os.makedirs(out_dir, exist_ok=True)
@@ -96,5 +144,11 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
         if len(pts) >= 2:
             c, d = fit_exponent([a for a, _ in pts], [v for _, v in pts])
             fits[p] = {"c_bits": c, "d": d, "points": pts}
+            rpts = sorted((n, results[(n, p)]["median_running_time"]) for n in ns
+                          if (n, p) in results and "median_running_time" in results[(n, p)])
+            if len(rpts) >= 2:
+                cr, dr = fit_exponent([a for a, _ in rpts], [v for _, v in rpts])
+                fits[p].update({"running_time_c_bits": cr, "running_time_d": dr, "running_time_points": rpts})
     return {"results": results, "fits": fits, "random_assignment_bits": random_assignment_exponent_bits(k, r),
-            "amp_layer_per_s": amp_layers / t_gpu if t_gpu else None, "gpu_seconds": t_gpu}
+            "amp_layer_per_s": amp_layers / t_gpu if t_gpu else None, "gpu_seconds": t_gpu,
+            "running_time_seconds": t_rt}

@@ -5,7 +5,8 @@
   one request per launch on the same GPU;
 * ``grad``:   batched adjoint gradients (256 instances, n = 22, p = 20) checked
   against central differences, then Adam on the shared angles;
-* ``sweep``:  median 1/p_succ versus n and its fitted exponent;
+* ``sweep``:  median 1/p_succ versus n and its fitted exponent, and the median
+  running time (bitstrings sampled until one satisfies) beside 1/E[p_succ];
 * ``batch``:  100 small instances (n = 12, p = 5, complex128) in one launch.
 
 Every function returns a JSON-serialisable dict.  All device work goes through
@@ -108,13 +109,23 @@ def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 
             "gamma_final": list(map(float, g1)), "beta_final": list(map(float, b1))}
 
 
-def sweep_workload(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, out_dir=None) -> dict:
-    res = sweep.run_sweep(ns=ns, ps=ps, seeds=seeds, out_dir=out_dir, log=None)
+def sweep_workload(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, out_dir=None,
+                   running_times: bool = True) -> dict:
+    res = sweep.run_sweep(ns=ns, ps=ps, seeds=seeds, out_dir=out_dir, log=None, running_times=running_times)
     table = {f"n{n}_p{p}": r["median_inv_psucc"] for (n, p), r in sorted(res["results"].items())}
-    return {"seeds": seeds, "ns": list(ns), "ps": list(ps), "median_inv_psucc": table,
-            "fits_bits": {str(p): {"c": f["c_bits"], "d": f["d"]} for p, f in res["fits"].items()},
-            "random_assignment_bits": res["random_assignment_bits"],
-            "amp_layer_per_s": res["amp_layer_per_s"], "gpu_seconds": res["gpu_seconds"]}
+    out = {"seeds": seeds, "ns": list(ns), "ps": list(ps), "median_inv_psucc": table,
+           "fits_bits": {str(p): {"c": f["c_bits"], "d": f["d"]} for p, f in res["fits"].items()},
+           "random_assignment_bits": res["random_assignment_bits"],
+           "amp_layer_per_s": res["amp_layer_per_s"], "gpu_seconds": res["gpu_seconds"]}
+    if running_times:
+        out["median_running_time"] = {f"n{n}_p{p}": r.get("median_running_time")
+                                      for (n, p), r in sorted(res["results"].items())}
+        out["inv_mean_psucc"] = {f"n{n}_p{p}": r.get("inv_mean_psucc") for (n, p), r in sorted(res["results"].items())}
+        out["censored_running_times"] = sum(r.get("censored_running_times", 0) for r in res["results"].values())
+        out["running_time_fits_bits"] = {str(p): {"c": f.get("running_time_c_bits"), "d": f.get("running_time_d")}
+                                         for p, f in res["fits"].items()}
+        out["running_time_seconds"] = res["running_time_seconds"]
+    return out
 
 
 def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p: int = 5, reps: int = 20) -> dict:

@@ -163,3 +163,21 @@ def test_full_size_draws_satisfy_the_definition():
     assert np.all(np.diff(xs[order].astype(np.int64)) >= 0)
     del state, cost
     torch.cuda.empty_cache()
+
+
+def test_sweep_reports_running_times(tmp_path):
+    """The scaling sweep's plumbing: per (n, p) median 1/p_succ and median
+    running time over instances, no censored instance at these sizes, the
+    results resumable from their files, and the exponents fitted."""
+    from paper_2401_02852_gb300 import sweep
+
+    res = sweep.run_sweep(ns=(14, 16), ps=(1, 4), seeds=12, out_dir=str(tmp_path), log=None, running_times=True)
+    for (n, p), r in res["results"].items():
+        rts = np.array(r["running_times"])
+        assert rts.size == 12 and np.all(rts >= 1) and r["censored_running_times"] == 0
+        assert r["median_running_time"] == np.median(rts)
+        assert r["inv_mean_psucc"] == pytest.approx(1.0 / np.mean(r["psucc"]))
+    for p in (1, 4):
+        assert "running_time_c_bits" in res["fits"][p]
+    again = sweep.run_sweep(ns=(14, 16), ps=(1, 4), seeds=12, out_dir=str(tmp_path), log=None, running_times=True)
+    assert again["results"][(16, 4)]["running_times"] == res["results"][(16, 4)]["running_times"]
