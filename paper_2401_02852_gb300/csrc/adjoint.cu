@@ -80,79 +80,107 @@ __device__ __forceinline__ void inv_round(typename G::V *vp, typename G::V *vl, 
     }
 }
 
-template <typename R, bool LOW, int NT>
+// State offset of register r's tile element in mapping LO: its row part plus
+// its group part times gstride = 2^lo (ROW: the tile's contiguous bits).
+template <int LO, int ROW>
+__device__ __forceinline__ uint32_t reg_off(int r, uint32_t gstride) {
+    const uint32_t u = (uint32_t)r << LO;
+    return (u & ((1u << ROW) - 1u)) + (u >> ROW) * gstride;
+}
+
+// One backward pass over the tiles of both states.  The tile pair (psi, lam)
+// and, in the low pass, the tile's cost bytes arrive by cp.async into dense
+// shared buffers; the next pair is copied as soon as the last exchange has been
+// read out, overlapping the last round, the phase and the stores.  HROW: row
+// bits of a high pass; FULL: every group bit of the tile is undone here (a
+// compile-time mask, straight-line stages); otherwise the runtime mask.
+template <typename R, bool LOW, int NT, int HROW, bool FULL>
 __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const __grid_constant__ AdjArgs<R> a,
                                                                         const __grid_constant__ AdjTab<R, NT> tab) {
     using G = AGeo<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
+    constexpr int LD = 8;  // load mapping: the registers on the top tile bits
     constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
+    constexpr int row = LOW ? T : HROW;
+    constexpr uint32_t full_mask = ((1u << T) - 1u) & ~(LOW ? 0u : (1u << row) - 1u);
+    const uint32_t active = FULL ? full_mask : a.active;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tp = reinterpret_cast<V *>(smem_raw);
     V *tl = tp + G::TILE_ELEMS;
-    V *stab = tl + G::TILE_ELEMS;
+    uint8_t *scs = reinterpret_cast<uint8_t *>(tl + G::TILE_ELEMS);  // low pass: 2 x 2^T cost bytes
+    V *stab = reinterpret_cast<V *>(scs + (LOW ? (2 << T) : 0));
     if (LOW) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
             V z;
             z.x = z.y = 0;
             stab[i] = i <= a.m ? tab.t[i] : z;
         }
-        __syncthreads();
     }
     const uint32_t tid = threadIdx.x;
     const size_t inst = blockIdx.y;
     V *psi = a.psi + (inst << a.n);
     V *lam = a.lam + (inst << a.n);
     const uint8_t *cs = a.cost + (inst << a.n);
-    const uint64_t ld_t = LOW ? tid : elem_offset(tile_elem<G, 8>(tid, 0), a.row, a.lo);
-    const uint64_t ld_s = LOW ? 256u : (1ull << (a.lo + 8 - a.row));
-    const uint64_t st_t = elem_offset(tile_elem<G, LC>(tid, 0), a.row, a.lo);
-    const uint64_t st_s = LOW ? (1ull << LC) : (1ull << (a.lo + LC - a.row));
+    const uint32_t st_t = elem_offset32(tile_elem<G, LC>(tid, 0), row, a.lo);
+    const uint32_t gstride = LOW ? 0u : (1u << a.lo);
+    const uint32_t tiles = (uint32_t)a.tiles;
+    auto issue = [&](uint32_t tt, uint8_t *scb) {
+        const uint32_t bb = tile_base32(tt, row, a.lo, T);
+        issue_tile<G>(psi, cs, bb, row, a.lo, true, LOW, tp, scb);
+        issue_tile<G>(lam, cs, bb, row, a.lo, true, false, tl, scb);
+    };
     double acc[2] = {0.0, 0.0};  // mixer term, phase term
-    for (uint64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
-        const uint64_t base = tile_base(t, a.row, a.lo, T);
+    uint32_t t = blockIdx.x;
+    if (t < tiles) issue(t, scs);
+    cp_async_commit();
+    for (int i = 0; t < tiles; ++i, t += gridDim.x) {
+        const int b = i & 1;
+        const uint8_t *sc = scs + ((size_t)b << T);
+        const uint32_t base = tile_base32(t, row, a.lo, T);
+        const uint32_t tn = t + gridDim.x;
+        cp_async_wait_all();
+        __syncthreads();
         V vp[NR], vl[NR];
-        {
-            const V *pp = psi + base + ld_t;
-            const V *pl = lam + base + ld_t;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                vp[r] = pp[r * ld_s];
-                vl[r] = pl[r * ld_s];
-            }
+        for (int r = 0; r < NR; ++r) {  // dense buffers, consecutive lanes: no conflicts
+            const uint32_t u = tile_elem<G, LD>(tid, r);
+            vp[r] = tp[u];
+            vl[r] = tl[u];
         }
         R term = 0;
-        inv_round<G, 8, T>(vp, vl, a.active, a.c, a.S, term);
+        inv_round<G, LD, T>(vp, vl, active, a.c, a.S, term);
         if (LOW) {
-            exchange<G, 8, 0>(vp, tp);
-            exchange<G, 8, 0>(vl, tl);
-            inv_round<G, 0, T>(vp, vl, a.active, a.c, a.S, term);
+            exchange<G, LD, 0>(vp, tp);
+            exchange<G, LD, 0>(vl, tl);
+            inv_round<G, 0, T>(vp, vl, active, a.c, a.S, term);
             exchange<G, 0, LC>(vp, tp);
             exchange<G, 0, LC>(vl, tl);
         } else {
-            exchange<G, 8, LC>(vp, tp);
-            exchange<G, 8, LC>(vl, tl);
+            exchange<G, LD, LC>(vp, tp);
+            exchange<G, LD, LC>(vl, tl);
         }
-        inv_round<G, LC, 8>(vp, vl, a.active, a.c, a.S, term);
+        __syncthreads();  // both buffers are read out: copy the next pair into them
+        if (tn < tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
+        cp_async_commit();
+        inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
         R gterm = 0;
-        {
-            V *pp = psi + base + st_t;
-            uint64_t ss = st_s;
-            asm volatile("" : "+l"(pp), "+l"(ss));  // keep the store addresses out of the load phase
-            V *pl = lam + base + st_t;
-            const uint8_t *pc = cs + base + st_t;
+        V *pp = psi + (base + st_t);
+        V *pl = lam + (base + st_t);
+        uint32_t gs = gstride;
+        asm volatile("" : "+l"(pp), "+l"(pl), "+r"(gs));  // keep the store addresses out of the load phase
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                if (LOW) {  // all of M_l undone: phase term, then D_l^dagger
-                    const int cst = __ldg(pc + r * ss);  // read-only path: no aliasing with the stores
-                    gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
-                    const V ph = stab[cst];
-                    vp[r] = cmul(vp[r], ph);
-                    vl[r] = cmul(vl[r], ph);
-                }
-                pp[r * ss] = vp[r];
-                pl[r * ss] = vl[r];
+        for (int r = 0; r < NR; ++r) {
+            if (LOW) {  // all of M_l undone: phase term, then D_l^dagger
+                const int cst = sc[tile_elem<G, LC>(tid, r)];
+                gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
+                const V ph = stab[cst];
+                vp[r] = cmul(vp[r], ph);
+                vl[r] = cmul(vl[r], ph);
             }
+            const uint32_t o = reg_off<LC, row>(r, gs);
+            pp[o] = vp[r];
+            pl[o] = vl[r];
         }
         acc[0] += (double)term;
         acc[1] += (double)gterm;
@@ -254,29 +282,54 @@ __global__ void __launch_bounds__(PT) small_grad_kernel(const uint8_t *costs, in
     }
 }
 
+// Dynamic shared memory of a backward pass: the two tile buffers, then (low
+// pass, m >= 0) two cost-byte buffers and the phase table.
 template <typename R>
 static size_t adj_smem(int m) {
-    return sizeof(typename AGeo<R>::V) * (2 * (size_t)AGeo<R>::TILE_ELEMS + (m < 0 ? 0 : (size_t)(m < 255 ? 256 : m + 1)));
+    using G = AGeo<R>;
+    size_t b = sizeof(typename G::V) * 2 * (size_t)G::TILE_ELEMS;
+    if (m >= 0) b += 2 * (size_t(1) << G::T) + sizeof(typename G::V) * (size_t)(m < 255 ? 256 : m + 1);
+    return b;
+}
+
+// Rows of a wide high group (complex64: 32 amplitudes, 256 B); complex128 rows
+// of 16 are 256 B already and take no wide groups.
+template <typename R>
+constexpr int adj_wrow() {
+    return sizeof(R) == 4 ? HIGH_ROW + 1 : HIGH_ROW;
 }
 
 template <typename R>
-static int adj_init() {
+struct AdjKernels {
+    using KF = void (*)(AdjArgs<R>, AdjTab<R, MAX_TABLE>);
+    using KN = void (*)(AdjArgs<R>, AdjTab<R, 1>);
+    KF low = adj_kernel<R, true, MAX_TABLE, HIGH_ROW, true>;
+    KN high[2][2] = {{adj_kernel<R, false, 1, HIGH_ROW, false>, adj_kernel<R, false, 1, HIGH_ROW, true>},
+                     {adj_kernel<R, false, 1, adj_wrow<R>(), false>, adj_kernel<R, false, 1, adj_wrow<R>(), true>}};
+};
+
+template <typename R>
+static int adj_init(AdjKernels<R> **out) {
     static std::mutex mu;
     static int state = 0;
+    static AdjKernels<R> ks;
     std::lock_guard<std::mutex> lk(mu);
     if (state == 0) {
-        const int big = (int)adj_smem<R>(QAOA_MAX_M);
-        cudaError_t e = cudaFuncSetAttribute(adj_kernel<R, true, MAX_TABLE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(adj_kernel<R, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaError_t e = cudaFuncSetAttribute(ks.low, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)adj_smem<R>(QAOA_MAX_M));
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+                e = cudaFuncSetAttribute(ks.high[w][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)adj_smem<R>(-1));
         const int small = (int)(2 * sizeof(typename Cx<R>::V) * (size_t(1) << Cx<R>::T) + (size_t(1) << Cx<R>::T));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(small_grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
         state = e == cudaSuccess ? 1 : -1;
         if (e != cudaSuccess) return cuda_error(e, "adjoint kernel attributes");
     }
-    return state > 0 ? QAOA_OK : set_error(QAOA_ECUDA, "adjoint kernels unavailable");
+    if (state < 0) return set_error(QAOA_ECUDA, "adjoint kernels unavailable");
+    *out = &ks;
+    return QAOA_OK;
 }
 
 template <typename R>
@@ -284,7 +337,8 @@ static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, cons
                        int dtype, int flags, void *state, void *adj, double *d_scr, double *h_scr,
                        cudaStream_t stream, double *p_succ, double *dgamma, double *dbeta) {
     using V = typename AGeo<R>::V;
-    int rc = adj_init<R>();
+    AdjKernels<R> *ks = nullptr;
+    int rc = adj_init<R>(&ks);
     if (rc) return rc;
     const int sign = (flags & QAOA_MIXER_RX2B) ? -1 : 1;
     // forward with the adjoint seed lam_p = P psi_p written by the last pass
@@ -303,7 +357,7 @@ static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, cons
     if ((rc = evolve_device_impl(r, stream, d_fpart, gxf))) return rc;
     QAOA_CUDA_TRY(cudaMemsetAsync(d_apart, 0, (size_t)batch * p * gxa * 2 * sizeof(double), stream));
     Plan pl;
-    if ((rc = make_plan_geo(n, AGeo<R>::T, 8, &pl))) return rc;
+    if ((rc = make_plan_geo(n, AGeo<R>::T, 8, &pl, false, adj_wrow<R>() != HIGH_ROW))) return rc;
     std::vector<char> tbuf(sizeof(AdjTab<R, MAX_TABLE>));
     auto *tab = reinterpret_cast<AdjTab<R, MAX_TABLE> *>(tbuf.data());
     AdjTab<R, 1> none{};
@@ -331,15 +385,17 @@ static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, cons
                 a.lo = AGeo<R>::T;
                 a.active = (1u << AGeo<R>::T) - 1u;
                 profile_before(K_ADJ_LOW, stream);
-                adj_kernel<R, true, MAX_TABLE>
-                    <<<dim3(gxa, batch), PT, adj_smem<R>(m), stream>>>(a, *tab);
+                ks->low<<<dim3(gxa, batch), PT, adj_smem<R>(m), stream>>>(a, *tab);
                 rc = profile_after(K_ADJ_LOW, stream);
             } else {
                 a.row = ps.row;
                 a.lo = ps.lo;
                 a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
+                if (ps.row != HIGH_ROW && ps.row != adj_wrow<R>())
+                    return set_error(QAOA_ECUDA, "adjoint plan: rows of %d bits", ps.row);
+                const int wide = ps.row != HIGH_ROW ? 1 : 0, full = ps.bits == pl.tile_bits - ps.row ? 1 : 0;
                 profile_before(K_ADJ_HIGH, stream);
-                adj_kernel<R, false, 1><<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);
+                ks->high[wide][full]<<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);
                 rc = profile_after(K_ADJ_HIGH, stream);
             }
             if (rc) return rc;
@@ -365,7 +421,8 @@ template <typename R>
 static int grad_small(int batch, int n, const uint8_t *cost, int m, int p, const double *gamma, const double *beta,
                       int flags, double *d_scr, double *h_scr, cudaStream_t stream, double *p_succ, double *dgamma,
                       double *dbeta) {
-    int rc = adj_init<R>();
+    AdjKernels<R> *ks = nullptr;
+    int rc = adj_init<R>(&ks);
     if (rc) return rc;
     const int sign = (flags & QAOA_MIXER_RX2B) ? -1 : 1;
     const size_t tab_n = (size_t)p * (m + 1);

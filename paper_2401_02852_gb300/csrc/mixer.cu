@@ -153,49 +153,6 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
     }
 }
 
-// cp.async (LDGSTS) helpers: 16-byte global -> shared copies that complete in
-// the background; completion is a hardware wait on the thread's commit groups.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Issues the copies of tile `base` into (buf, sc): the state as 16-byte chunks
-// (the tile's rows of 2^row amplitudes are whole numbers of chunks) and, when
-// needed, its cost bytes (one 16-byte chunk per row of 16 amplitudes).  Chunk q
-// of the tile lands at byte 16 q of the buffer, i.e. tile element u sits at
-// buf[u]; thread tid takes chunks tid + PT j, whose addresses are a thread
-// base plus j times a stride.
-template <typename R, bool LOW>
-__device__ __forceinline__ void issue_tile(const typename Cx<R>::V *st, const uint8_t *cs, uint32_t base, int row,
-                                           int lo, bool state, bool cost, typename Cx<R>::V *buf, uint8_t *sc) {
-    using V = typename Cx<R>::V;
-    constexpr int T = Cx<R>::T;
-    constexpr int EPC = 16 / (int)sizeof(V);            // amplitudes per 16-byte chunk
-    constexpr int NT = Cx<R>::PT;
-    constexpr int NCH = (1 << T) / EPC / NT;             // state chunks per thread
-    constexpr int CCH = (1 << T) / 16 / NT;              // cost chunks per thread
-    const uint32_t tid = threadIdx.x;
-    if (state) {
-        // chunk q = tid + PT j covers tile elements [EPC q, EPC q + EPC)
-        // the bits of EPC * NT * j lie above those of EPC * tid and above the row
-        // bits, so the offset is linear in j
-        const uint32_t off0 = base + elem_offset32((uint32_t)EPC * tid, row, lo);
-        const uint32_t step = elem_offset32((uint32_t)(EPC * NT), row, lo);
-        char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * NT * j, st + (off0 + step * j));
-    }
-    if (cost) {
-        const uint32_t off0 = base + elem_offset32(16u * tid, row, lo);
-        const uint32_t step = elem_offset32(16u * NT, row, lo);
-#pragma unroll
-        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + NT * j), cs + (off0 + step * j));
-    }
-}
-
 // Halved state, low pass: the tile is the half-tile [base, base + H) and its
 // mirror block [mbase, mbase + H), H = 2^(T-1), each copied in memory order
 // (the mirror block lands at positions [H, 2H)).
@@ -272,7 +229,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         if (Z2)
             issue_tile_z2<R>(st, cs, bb, M - bb - (H - 1), need_s, need_c, tile, scb);
         else
-            issue_tile<R, LOW>(st, cs, bb, row, a.lo, need_s, need_c, tile, scb);
+            issue_tile<Cx<R>>(st, cs, bb, row, a.lo, need_s, need_c, tile, scb);
     };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     const uint32_t tiles = (uint32_t)a.tiles;

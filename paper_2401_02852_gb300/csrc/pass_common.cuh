@@ -219,6 +219,49 @@ __device__ __forceinline__ void exchange(typename G::V *v, typename G::V *tile) 
     for (int r = 0; r < NR; ++r) v[r] = pt[G::swz((uint32_t)r << TO)];
 }
 
+// cp.async (LDGSTS) helpers: 16-byte global -> shared copies that complete in
+// the background; completion is a hardware wait on the thread's commit groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issues the copies of tile `base` into (buf, sc): the state as 16-byte chunks
+// (the tile's rows of 2^row amplitudes are whole numbers of chunks) and, when
+// needed, its cost bytes (one 16-byte chunk per row of 16 amplitudes).  Chunk q
+// of the tile lands at byte 16 q of the buffer, i.e. tile element u sits at
+// buf[u]; thread tid takes chunks tid + PT j, whose addresses are a thread
+// base plus j times a stride.  Indices inside one instance fit in 32 bits.
+template <typename G>
+__device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_t *cs, uint32_t base, int row, int lo,
+                                           bool state, bool cost, typename G::V *buf, uint8_t *sc) {
+    using V = typename G::V;
+    constexpr int T = G::T;
+    constexpr int EPC = 16 / (int)sizeof(V);            // amplitudes per 16-byte chunk
+    constexpr int NT = G::PT;
+    constexpr int NCH = (1 << T) / EPC / NT;             // state chunks per thread
+    constexpr int CCH = (1 << T) / 16 / NT;              // cost chunks per thread
+    const uint32_t tid = threadIdx.x;
+    if (state) {
+        // chunk q = tid + PT j covers tile elements [EPC q, EPC q + EPC)
+        // the bits of EPC * NT * j lie above those of EPC * tid and above the row
+        // bits, so the offset is linear in j
+        const uint32_t off0 = base + elem_offset32((uint32_t)EPC * tid, row, lo);
+        const uint32_t step = elem_offset32((uint32_t)(EPC * NT), row, lo);
+        char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * NT * j, st + (off0 + step * j));
+    }
+    if (cost) {
+        const uint32_t off0 = base + elem_offset32(16u * tid, row, lo);
+        const uint32_t step = elem_offset32(16u * NT, row, lo);
+#pragma unroll
+        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + NT * j), cs + (off0 + step * j));
+    }
+}
+
 // FP64 block reduction of NV values per thread (NT threads); thread 0 gets
 // the sums.
 template <int NV, int NT = PT>

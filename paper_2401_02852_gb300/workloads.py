@@ -70,10 +70,33 @@ def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 
             torch.empty((batch, 1 << n), dtype=torch.complex64, device="cuda"))
     api.grad_batch(n, costs, m, g0, b0, "c64", work=work)  # warm-up
     _sync()
-    t0 = time.perf_counter()
-    ps, dg, db = api.grad_batch(n, costs, m, g0, b0, "c64", work=work)
-    _sync()
-    t_grad = time.perf_counter() - t0
+    with api.Profiler() as prof:
+        t0 = time.perf_counter()
+        ps, dg, db = api.grad_batch(n, costs, m, g0, b0, "c64", work=work)
+        _sync()
+        t_grad = time.perf_counter() - t0
+    # per-kind roofline: algorithmic bytes of each launch kind over its event time
+    es, N = 8, batch * (1 << n)
+    kinds = prof.stats
+    roof = {}
+    for kind, (count, ms) in kinds.items():
+        if kind in ("adjoint_low", "adjoint_high"):
+            per = 4 * es * N + (N if kind == "adjoint_low" else 0)  # psi and lam read + written (+ C)
+        elif kind in ("pass_low", "pass_high"):
+            per = None  # forward passes: counted from the schedule below
+        else:
+            continue
+        if per:
+            roof[kind] = {"launches": count, "ms": ms, "GBps": per * count / (ms * 1e-3) / 1e9}
+    fwd_bytes = 0
+    seq = api.pass_schedule(n, p, "c64")
+    for i, (pi, _, mode) in enumerate(seq):
+        last = i + 1 == len(seq)
+        fwd_bytes += N * (es + 1) if mode == 0 else N * 2 * es + (N if mode in (2, 3) or last else 0)
+        if last:
+            fwd_bytes += N * es  # the adjoint seed lam_p = P psi_p written beside the state
+    fwd_ms = sum(kinds.get(k, (0, 0.0))[1] for k in ("pass_low", "pass_high"))
+    roof["forward"] = {"launches": len(seq), "ms": fwd_ms, "GBps": fwd_bytes / (fwd_ms * 1e-3) / 1e9}
     # central differences (h = 1e-4) on the complex128 evolution of a few instances
     fd = []
     h = 1e-4
@@ -101,7 +124,19 @@ def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 
     t_adam = time.perf_counter() - t0
     # one gradient = forward (p layers) + reverse sweep (p layers on two states)
     amp_layers = batch * (1 << n) * p
-    return {"batch": batch, "n": n, "m": m, "p": p, "grad_seconds": t_grad,
+    peak = None
+    try:
+        import json as _json
+        import os as _os
+        with open(_os.path.join(_os.path.dirname(_os.path.dirname(_os.path.abspath(__file__))),
+                                "MEASURED_PEAKS.json")) as f:
+            peak = float(_json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
+    if peak:
+        for v in roof.values():
+            v["frac_of_measured_peak"] = v["GBps"] / peak
+    return {"batch": batch, "n": n, "m": m, "p": p, "grad_seconds": t_grad, "roofline_by_kind": roof,
             "grad_amp_layer_per_s_forward_equiv": amp_layers / t_grad, "mean_psucc_initial": float(np.mean(ps)),
             "fd_checks": fd, "adam_steps": adam_steps, "adam_seconds": t_adam,
             "objective_first": trace[0][1], "objective_last": trace[-1][1],
