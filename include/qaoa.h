@@ -292,6 +292,18 @@ int qaoa_plan(int n, int dtype, int flags, int *group_lo, int *group_bits, int *
 int qaoa_pass_schedule(int n, int p, int dtype, int flags, int max_launches, int *pass_index, int *layer,
                        int *mode);
 
+/* The launch sequence of the gradient's backward sweep (layers p-1 down to 0;
+ * the passes are those of the backward plan: 2^12-amplitude tiles of both
+ * states, groups of at most 8 bits).  For launch i: its pass (0 = low), its
+ * layer l and its mode (0: undo the butterflies of layer l on the group;
+ * 1: then take the phase term of layer l and undo its phase; 2: then also
+ * undo the butterflies of layer l - 1 on the same group).  The phase of a
+ * layer is undone only after all its butterflies (every qubit factor
+ * commutes with the others, not with the phase).  Returns the number of
+ * launches (P + (p - 1)(P - 1) for P passes per layer when every boundary
+ * fuses) or an error; host only. */
+int qaoa_adjoint_schedule(int n, int p, int dtype, int max_launches, int *pass_index, int *layer, int *mode);
+
 /* Per-kernel timing: when enabled, every kernel the library launches is
  * bracketed by CUDA events on its stream.  qaoa_profile_read synchronises the
  * device, then returns for kernel kind i (names via qaoa_kernel_name) the

@@ -73,6 +73,7 @@ SIGNATURES = {
     "qaoa_server_destroy": (I, [P]),
     "qaoa_plan": (I, [I, I, I, P, P, P]),
     "qaoa_pass_schedule": (I, [I, I, I, I, I, P, P, P]),
+    "qaoa_adjoint_schedule": (I, [I, I, I, I, P, P, P]),
     "qaoa_profile_enable": (I, [I]),
     "qaoa_profile_read": (I, [I, P, P]),
     "qaoa_kernel_name": (ctypes.c_char_p, [I]),

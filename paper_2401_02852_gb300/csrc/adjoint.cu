@@ -35,10 +35,12 @@ template <typename R>
 struct AdjArgs {
     typename AGeo<R>::V *psi, *lam;
     const uint8_t *cost;
-    double *partials;  // this layer's slice: [batch][p][gx][2], base at layer l
+    double *partials;   // layer l's slice: [batch][p][gx][2], base at layer l
+    double *partials2;  // A_FUSED: layer l - 1's slice (nullable: no second layer)
     int n, row, lo, m, p;
     uint32_t active;
-    R c, S;            // inverse butterfly coefficients
+    R c, S;             // inverse butterfly coefficients of layer l
+    R c2, S2;           // A_FUSED: those of layer l - 1
     uint64_t tiles;
 };
 
@@ -89,14 +91,22 @@ __device__ __forceinline__ uint32_t reg_off(int r, uint32_t gstride) {
 }
 
 // One backward pass over the tiles of both states.  The tile pair (psi, lam)
-// and, in the low pass, the tile's cost bytes arrive by cp.async into dense
-// shared buffers; the next pair is copied as soon as the last exchange has been
-// read out, overlapping the last round, the phase and the stores.  HROW: row
-// bits of a high pass; FULL: every group bit of the tile is undone here (a
-// compile-time mask, straight-line stages); otherwise the runtime mask.
-template <typename R, bool LOW, int NT, int HROW, bool FULL>
+// and, when the pass undoes a phase, the tile's cost bytes arrive by cp.async
+// into dense shared buffers; the next pair is copied as soon as the last
+// exchange has been read out, overlapping the last round, the phase and the
+// stores.  MODE (AdjMode): A_PLAIN undoes layer l's butterflies on the group;
+// A_PHASE then takes the phase term and undoes D_l; A_FUSED (high passes) also
+// undoes layer l-1's butterflies on the same group, in the mapping it ends in
+// and back (with c2 = 1, S2 = 0 and no partials2 it is A_PHASE for a high
+// group).  HROW: row bits of a high pass; FULL: every group bit of the tile is
+// undone here (a compile-time mask, straight-line stages), else the runtime
+// mask.
+template <typename R, bool LOW, int MODE, int NT, int HROW, bool FULL>
 __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const __grid_constant__ AdjArgs<R> a,
                                                                         const __grid_constant__ AdjTab<R, NT> tab) {
+    static_assert(!LOW || MODE != A_FUSED, "the low pass never fuses");
+    static_assert(LOW || MODE != A_PHASE, "a high pass undoes a phase in its fused form");
+    constexpr bool PH = MODE != A_PLAIN;  // the pass undoes a phase
     using G = AGeo<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
@@ -108,9 +118,9 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tp = reinterpret_cast<V *>(smem_raw);
     V *tl = tp + G::TILE_ELEMS;
-    uint8_t *scs = reinterpret_cast<uint8_t *>(tl + G::TILE_ELEMS);  // low pass: 2 x 2^T cost bytes
-    V *stab = reinterpret_cast<V *>(scs + (LOW ? (2 << T) : 0));
-    if (LOW) {  // 256 entries at least: any uint8 cost indexes inside the table
+    uint8_t *scs = reinterpret_cast<uint8_t *>(tl + G::TILE_ELEMS);  // phase passes: 2 x 2^T cost bytes
+    V *stab = reinterpret_cast<V *>(scs + (PH ? (2 << T) : 0));
+    if (PH) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {
             V z;
             z.x = z.y = 0;
@@ -122,15 +132,16 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
     V *psi = a.psi + (inst << a.n);
     V *lam = a.lam + (inst << a.n);
     const uint8_t *cs = a.cost + (inst << a.n);
-    const uint32_t st_t = elem_offset32(tile_elem<G, LC>(tid, 0), row, a.lo);
+    constexpr int SM = MODE == A_FUSED ? LD : LC;  // store mapping
+    const uint32_t st_t = elem_offset32(tile_elem<G, SM>(tid, 0), row, a.lo);
     const uint32_t gstride = LOW ? 0u : (1u << a.lo);
     const uint32_t tiles = (uint32_t)a.tiles;
     auto issue = [&](uint32_t tt, uint8_t *scb) {
         const uint32_t bb = tile_base32(tt, row, a.lo, T);
-        issue_tile<G>(psi, cs, bb, row, a.lo, true, LOW, tp, scb);
+        issue_tile<G>(psi, cs, bb, row, a.lo, true, PH, tp, scb);
         issue_tile<G>(lam, cs, bb, row, a.lo, true, false, tl, scb);
     };
-    double acc[2] = {0.0, 0.0};  // mixer term, phase term
+    double acc[3] = {0.0, 0.0, 0.0};  // mixer term, phase term (layer l), mixer term (layer l - 1)
     uint32_t t = blockIdx.x;
     if (t < tiles) issue(t, scs);
     cp_async_commit();
@@ -148,7 +159,23 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
             vp[r] = tp[u];
             vl[r] = tl[u];
         }
-        R term = 0;
+        R term = 0, gterm = 0, term2 = 0;
+        auto prefetch = [&]() {  // both buffers are read out: copy the next pair into them
+            __syncthreads();
+            if (tn < tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
+            cp_async_commit();
+        };
+        // all of M_l undone on this tile: phase term, then D_l^dagger (mapping LC)
+        auto undo_phase = [&]() {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int cst = sc[tile_elem<G, LC>(tid, r)];
+                gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
+                const V ph = stab[cst];
+                vp[r] = cmul(vp[r], ph);
+                vl[r] = cmul(vl[r], ph);
+            }
+        };
         inv_round<G, LD, T>(vp, vl, active, a.c, a.S, term);
         if (LOW) {
             exchange<G, LD, 0>(vp, tp);
@@ -156,40 +183,45 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
             inv_round<G, 0, T>(vp, vl, active, a.c, a.S, term);
             exchange<G, 0, LC>(vp, tp);
             exchange<G, 0, LC>(vl, tl);
+            prefetch();
+            inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
+            if (PH) undo_phase();
+        } else if (MODE == A_FUSED) {
+            exchange<G, LD, LC>(vp, tp);
+            exchange<G, LD, LC>(vl, tl);
+            inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
+            undo_phase();
+            inv_round<G, LC, LD>(vp, vl, active, a.c2, a.S2, term2);
+            exchange<G, LC, LD>(vp, tp);
+            exchange<G, LC, LD>(vl, tl);
+            prefetch();
+            inv_round<G, LD, T>(vp, vl, active, a.c2, a.S2, term2);
         } else {
             exchange<G, LD, LC>(vp, tp);
             exchange<G, LD, LC>(vl, tl);
+            prefetch();
+            inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
         }
-        __syncthreads();  // both buffers are read out: copy the next pair into them
-        if (tn < tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
-        cp_async_commit();
-        inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
-        R gterm = 0;
         V *pp = psi + (base + st_t);
         V *pl = lam + (base + st_t);
         uint32_t gs = gstride;
         asm volatile("" : "+l"(pp), "+l"(pl), "+r"(gs));  // keep the store addresses out of the load phase
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            if (LOW) {  // all of M_l undone: phase term, then D_l^dagger
-                const int cst = sc[tile_elem<G, LC>(tid, r)];
-                gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
-                const V ph = stab[cst];
-                vp[r] = cmul(vp[r], ph);
-                vl[r] = cmul(vl[r], ph);
-            }
-            const uint32_t o = reg_off<LC, row>(r, gs);
+            const uint32_t o = reg_off<SM, row>(r, gs);
             pp[o] = vp[r];
             pl[o] = vl[r];
         }
         acc[0] += (double)term;
         acc[1] += (double)gterm;
+        acc[2] += (double)term2;
     }
-    block_sum<2>(acc);
+    block_sum<3>(acc);
     if (threadIdx.x == 0) {
-        double *out = a.partials + 2 * ((inst * a.p) * gridDim.x + blockIdx.x);
-        out[0] += acc[0];
-        out[1] += acc[1];
+        const size_t slot = 2 * ((inst * a.p) * gridDim.x + blockIdx.x);
+        a.partials[slot] += acc[0];
+        a.partials[slot + 1] += acc[1];
+        if (MODE == A_FUSED && a.partials2) a.partials2[slot] += acc[2];
     }
 }
 
@@ -303,9 +335,15 @@ template <typename R>
 struct AdjKernels {
     using KF = void (*)(AdjArgs<R>, AdjTab<R, MAX_TABLE>);
     using KN = void (*)(AdjArgs<R>, AdjTab<R, 1>);
-    KF low = adj_kernel<R, true, MAX_TABLE, HIGH_ROW, true>;
-    KN high[2][2] = {{adj_kernel<R, false, 1, HIGH_ROW, false>, adj_kernel<R, false, 1, HIGH_ROW, true>},
-                     {adj_kernel<R, false, 1, adj_wrow<R>(), false>, adj_kernel<R, false, 1, adj_wrow<R>(), true>}};
+    static constexpr int W = adj_wrow<R>();
+    KN low = adj_kernel<R, true, A_PLAIN, 1, HIGH_ROW, true>;
+    KF low_phase = adj_kernel<R, true, A_PHASE, MAX_TABLE, HIGH_ROW, true>;
+    // [wide][full]
+    KN high[2][2] = {{adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, false>, adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, true>},
+                     {adj_kernel<R, false, A_PLAIN, 1, W, false>, adj_kernel<R, false, A_PLAIN, 1, W, true>}};
+    KF fused[2][2] = {
+        {adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, false>, adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, true>},
+        {adj_kernel<R, false, A_FUSED, MAX_TABLE, W, false>, adj_kernel<R, false, A_FUSED, MAX_TABLE, W, true>}};
 };
 
 template <typename R>
@@ -316,11 +354,18 @@ static int adj_init(AdjKernels<R> **out) {
     std::lock_guard<std::mutex> lk(mu);
     if (state == 0) {
         cudaError_t e = cudaFuncSetAttribute(ks.low, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)adj_smem<R>(QAOA_MAX_M));
+                                             (int)adj_smem<R>(-1));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ks.low_phase, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)adj_smem<R>(QAOA_MAX_M));
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+            for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
                 e = cudaFuncSetAttribute(ks.high[w][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)adj_smem<R>(-1));
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(ks.fused[w][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)adj_smem<R>(QAOA_MAX_M));
+            }
         const int small = (int)(2 * sizeof(typename Cx<R>::V) * (size_t(1) << Cx<R>::T) + (size_t(1) << Cx<R>::T));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(small_grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
@@ -361,45 +406,62 @@ static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, cons
     std::vector<char> tbuf(sizeof(AdjTab<R, MAX_TABLE>));
     auto *tab = reinterpret_cast<AdjTab<R, MAX_TABLE> *>(tbuf.data());
     AdjTab<R, 1> none{};
-    for (int l = p - 1; l >= 0; --l) {
+    const std::vector<Launch> seq = make_adj_schedule(pl.n_passes, p);
+    for (const Launch &L : seq) {
+        const int l = L.la;
+        const Pass &ps = pl.pass[L.pass];
         const double c = std::cos(beta[l]), S = sign * std::sin(beta[l]);
-        for (int k = 0; k <= m; ++k) {
-            tab->t[k].x = (R)std::cos(gamma[l] * k);
-            tab->t[k].y = (R)std::sin(gamma[l] * k);
-        }
-        for (int i = pl.n_passes - 1; i >= 0; --i) {
-            const Pass &ps = pl.pass[i];
-            AdjArgs<R> a;
-            a.psi = reinterpret_cast<V *>(state);
-            a.lam = reinterpret_cast<V *>(adj);
-            a.cost = cost;
-            a.partials = d_apart + (size_t)l * gxa * 2;
-            a.n = n;
-            a.m = m;
-            a.p = p;
-            a.c = (R)c;
-            a.S = (R)S;
-            a.tiles = tiles;
-            if (i == 0) {
-                a.row = AGeo<R>::T;
-                a.lo = AGeo<R>::T;
-                a.active = (1u << AGeo<R>::T) - 1u;
-                profile_before(K_ADJ_LOW, stream);
-                ks->low<<<dim3(gxa, batch), PT, adj_smem<R>(m), stream>>>(a, *tab);
-                rc = profile_after(K_ADJ_LOW, stream);
-            } else {
-                a.row = ps.row;
-                a.lo = ps.lo;
-                a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
-                if (ps.row != HIGH_ROW && ps.row != adj_wrow<R>())
-                    return set_error(QAOA_ECUDA, "adjoint plan: rows of %d bits", ps.row);
-                const int wide = ps.row != HIGH_ROW ? 1 : 0, full = ps.bits == pl.tile_bits - ps.row ? 1 : 0;
-                profile_before(K_ADJ_HIGH, stream);
-                ks->high[wide][full]<<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);
-                rc = profile_after(K_ADJ_HIGH, stream);
+        AdjArgs<R> a;
+        a.psi = reinterpret_cast<V *>(state);
+        a.lam = reinterpret_cast<V *>(adj);
+        a.cost = cost;
+        a.partials = d_apart + (size_t)l * gxa * 2;
+        a.partials2 = nullptr;
+        a.n = n;
+        a.m = m;
+        a.p = p;
+        a.c = (R)c;
+        a.S = (R)S;
+        a.c2 = (R)1;  // identity second half unless the pass fuses layer l - 1
+        a.S2 = (R)0;
+        a.tiles = tiles;
+        if (L.mode != A_PLAIN) {
+            for (int k = 0; k <= m; ++k) {  // D_l^dagger = exp(+i gamma_l C)
+                tab->t[k].x = (R)std::cos(gamma[l] * k);
+                tab->t[k].y = (R)std::sin(gamma[l] * k);
             }
-            if (rc) return rc;
         }
+        if (L.mode == A_FUSED) {
+            a.c2 = (R)std::cos(beta[l - 1]);
+            a.S2 = (R)(sign * std::sin(beta[l - 1]));
+            a.partials2 = d_apart + (size_t)(l - 1) * gxa * 2;
+        }
+        if (L.pass == 0) {
+            a.row = AGeo<R>::T;
+            a.lo = AGeo<R>::T;
+            a.active = (1u << AGeo<R>::T) - 1u;
+            if (L.mode == A_FUSED) return set_error(QAOA_ECUDA, "adjoint schedule: fused low pass");
+            profile_before(K_ADJ_LOW, stream);
+            if (L.mode == A_PHASE)
+                ks->low_phase<<<dim3(gxa, batch), PT, adj_smem<R>(m), stream>>>(a, *tab);
+            else
+                ks->low<<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);
+            rc = profile_after(K_ADJ_LOW, stream);
+        } else {
+            a.row = ps.row;
+            a.lo = ps.lo;
+            a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
+            if (ps.row != HIGH_ROW && ps.row != adj_wrow<R>())
+                return set_error(QAOA_ECUDA, "adjoint plan: rows of %d bits", ps.row);
+            const int wide = ps.row != HIGH_ROW ? 1 : 0, full = ps.bits == pl.tile_bits - ps.row ? 1 : 0;
+            profile_before(K_ADJ_HIGH, stream);
+            if (L.mode == A_PLAIN)
+                ks->high[wide][full]<<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);
+            else  // A_FUSED, or A_PHASE as the fused kernel with an identity second layer
+                ks->fused[wide][full]<<<dim3(gxa, batch), PT, adj_smem<R>(m), stream>>>(a, *tab);
+            rc = profile_after(K_ADJ_HIGH, stream);
+        }
+        if (rc) return rc;
     }
     if ((rc = launch_reduce(d_apart, batch * p, gxa, 2, d_ares, stream))) return rc;
     QAOA_CUDA_TRY(cudaMemcpyAsync(h_scr, d_fres, (size_t)batch * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));

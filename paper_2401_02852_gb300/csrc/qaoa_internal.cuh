@@ -110,6 +110,16 @@ struct Launch {
 enum PassMode { MODE_INIT = 0, MODE_PLAIN = 1, MODE_FUSED = 2, MODE_PHASE = 3 };
 std::vector<Launch> make_schedule(int n_passes, int p);
 
+// The backward (adjoint) sweep, layers p-1 down to 0.  Each launch undoes the
+// butterflies of layer la on one group; the last pass of a layer also takes
+// the phase term and undoes D_la (A_PHASE), and when layer la - 1 starts with
+// the same group it goes on to undo that layer's butterflies too (A_FUSED).
+// With two or more high groups the orders alternate ([1, 0, 2, ..., k] and
+// [k, 0, k-1, ..., 1]) so every layer boundary fuses on a high group; with one
+// high group each layer is [1, 0] with the phase in the low pass.
+enum AdjMode { A_PLAIN = 0, A_PHASE = 1, A_FUSED = 2 };
+std::vector<Launch> make_adj_schedule(int n_passes, int p);
+
 // ---------------------------------------------------------------------------
 // Host-side per-layer coefficients.  One mixer layer is
 //   prod_j [c I + i S X_j] = sigma^n prod_j [A I + i B X_j]

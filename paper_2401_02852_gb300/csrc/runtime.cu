@@ -234,6 +234,34 @@ std::vector<Launch> make_schedule(int n_passes, int p) {
     return out;
 }
 
+std::vector<Launch> make_adj_schedule(int n_passes, int p) {
+    std::vector<Launch> out;
+    const int k = n_passes - 1;
+    std::vector<int> even, odd;
+    if (k >= 2) {
+        even.push_back(1);
+        even.push_back(0);
+        for (int g = 2; g <= k; ++g) even.push_back(g);
+        odd.push_back(k);
+        odd.push_back(0);
+        for (int g = k - 1; g >= 1; --g) odd.push_back(g);
+    } else {
+        even = {1, 0};
+        odd = {1, 0};
+    }
+    for (int j = 0; j < p; ++j) {  // j-th layer undone: la = p - 1 - j
+        const int la = p - 1 - j;
+        const std::vector<int> &ord = (j % 2 == 0) ? even : odd;
+        for (int q = 0; q < n_passes; ++q) {
+            if (k >= 2 && j > 0 && q == 0) continue;  // undone by the previous layer's fused pass
+            int mode = A_PLAIN;
+            if (q == n_passes - 1) mode = (k >= 2 && la > 0) ? A_FUSED : A_PHASE;
+            out.push_back({ord[q], la, mode});
+        }
+    }
+    return out;
+}
+
 LayerCoef layer_coef(double beta, int sign) {
     const double c = std::cos(beta), sn = std::sin(beta);
     const double S = sign * sn;  // butterfly: a' = c a + i S b, b' = i S a + c b
@@ -290,6 +318,24 @@ int qaoa_pass_schedule(int n, int p, int dtype, int flags, int max_launches, int
     int rc = make_plan(n, dtype, &pl, (flags & QAOA_Z2_HALF) != 0);
     if (rc) return rc;
     const std::vector<Launch> seq = make_schedule(pl.n_passes, p);
+    for (size_t i = 0; i < seq.size() && (int)i < max_launches; ++i) {
+        if (pass_index) pass_index[i] = seq[i].pass;
+        if (layer) layer[i] = seq[i].la;
+        if (mode) mode[i] = seq[i].mode;
+    }
+    return (int)seq.size();
+}
+
+extern "C" int qaoa_adjoint_schedule(int n, int p, int dtype, int max_launches, int *pass_index, int *layer,
+                                     int *mode) {
+    if (p < 1) return set_error(QAOA_EINVAL, "p=%d", p);
+    if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", dtype);
+    Plan pl;
+    // the backward passes tile both states in 2^12-amplitude tiles, groups of
+    // at most 8 bits (complex64 also takes 7-bit groups with 256-byte rows)
+    int rc = make_plan_geo(n, 12, 8, &pl, false, dtype == QAOA_C64);
+    if (rc) return rc;
+    const std::vector<Launch> seq = make_adj_schedule(pl.n_passes, p);
     for (size_t i = 0; i < seq.size() && (int)i < max_launches; ++i) {
         if (pass_index) pass_index[i] = seq[i].pass;
         if (layer) layer[i] = seq[i].la;

@@ -158,3 +158,34 @@ def test_schedule_applies_each_layer_in_order(lib, dtype, T, p, z2):
                 assert l == layer and q not in seen
                 seen.append(q)
         assert layer == p - 1 and sorted(seen) == list(range(n))
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n,p", [(13, 1), (13, 4), (20, 3), (22, 20), (30, 10), (32, 5)])
+def test_adjoint_schedule_undoes_each_layer_in_reverse(lib, dtype, n, p):
+    """Replays the backward sweep: layers p-1 .. 0 in turn; every pass undoes
+    each layer's butterflies exactly once, and the layer's phase goes after all
+    of them (mode 1 or 2 on its last pass); a fused launch (mode 2) goes on to
+    undo layer l - 1 on the same group, so that layer skips it."""
+    cap = 8 * p + 8
+    idx, lay, mod = (ctypes.c_int * cap)(), (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+    k = lib.qaoa_adjoint_schedule(n, p, dtype, cap, idx, lay, mod)
+    assert k > 0
+    seq = [(idx[i], lay[i], mod[i]) for i in range(k)]
+    n_passes = max(s[0] for s in seq) + 1
+    undone = {l: [] for l in range(p)}
+    phase_done = []
+    for pi, l, mode in seq:
+        assert l not in phase_done and all(x in phase_done for x in range(l + 1, p))
+        undone[l].append(pi)
+        if mode in (1, 2):
+            assert sorted(undone[l]) == list(range(n_passes))  # the whole layer first
+            phase_done.append(l)
+        if mode == 2:
+            assert pi != 0 and l >= 1
+            undone[l - 1].append(pi)
+    assert phase_done == list(range(p - 1, -1, -1))
+    if n_passes >= 3:  # every boundary fuses: one launch saved per boundary
+        assert k == n_passes + (p - 1) * (n_passes - 1)
+    else:
+        assert k == 2 * p
