@@ -116,12 +116,8 @@ __device__ __forceinline__ uint32_t tile_elem(uint32_t tid, uint32_t r) {
     return (tid & ((1u << LO) - 1u)) | ((tid >> LO) << (LO + RB)) | (r << LO);
 }
 
-// State index of tile element u (relative to the tile base).
-__device__ __forceinline__ uint64_t elem_offset(uint32_t u, int row, int lo) {
-    return (uint64_t)(u & ((1u << row) - 1u)) | ((uint64_t)(u >> row) << lo);
-}
-
-// The same in 32 bits (state indices of one instance, n <= 32).
+// State index of tile element u relative to the tile base, in 32 bits (the
+// indices of one instance fit, n <= 32).
 __device__ __forceinline__ uint32_t elem_offset32(uint32_t u, int row, int lo) {
     return (u & ((1u << row) - 1u)) | ((u >> row) << lo);
 }

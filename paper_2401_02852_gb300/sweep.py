@@ -44,7 +44,8 @@ def sample_running_times(n: int, costs, states, flags: int, tag: str, first_k: i
                          max_draws: int = 1 << 26, draw_budget: int = 1 << 27):
     """Running time of every instance of a batch: rounds of k draws (k growing
     4x per round) for the instances still without a satisfying draw; an
-    instance still unresolved after `max_draws` draws is censored (-1)."""
+    instance still unresolved after `max_draws` draws is censored (-1).
+    Returns the running times and the number of draws taken."""
     B = states.shape[0]
     rt = np.zeros(B, dtype=np.int64)
     done = np.zeros(B, dtype=np.int64)  # draws taken so far
@@ -68,7 +69,7 @@ def sample_running_times(n: int, costs, states, flags: int, tag: str, first_k: i
         k *= 4
         rnd += 1
     rt[open_] = -1
-    return rt
+    return rt, int(done.sum())
 
 
 def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int = 5, r: float = 8.0,
@@ -79,6 +80,7 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
     amp_layers = 0
     t_gpu = 0.0
     t_rt = 0.0
+    draws = 0
     for n in ns:
         todo = [p for p in ps if not (out_dir and os.path.exists(os.path.join(out_dir, f"n{n}_p{p}.json")))]
         for p in ps:
@@ -115,8 +117,9 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
                 psucc[p].extend(float(x) for x in ps_b)
                 if running_times:
                     t1 = time.perf_counter()
-                    rts[p].extend(int(x) for x in sample_running_times(
-                        n, costs, states, api.Z2_HALF, f"rt-n{n}-p{p}-c{c0}"))
+                    rt_b, nd = sample_running_times(n, costs, states, api.Z2_HALF, f"rt-n{n}-p{p}-c{c0}")
+                    rts[p].extend(int(x) for x in rt_b)
+                    draws += nd
                     t_rt += time.perf_counter() - t1
             del states, costs
             torch.cuda.empty_cache()
@@ -151,4 +154,4 @@ def run_sweep(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, k: int =
                 fits[p].update({"running_time_c_bits": cr, "running_time_d": dr, "running_time_points": rpts})
     return {"results": results, "fits": fits, "random_assignment_bits": random_assignment_exponent_bits(k, r),
             "amp_layer_per_s": amp_layers / t_gpu if t_gpu else None, "gpu_seconds": t_gpu,
-            "running_time_seconds": t_rt}
+            "running_time_seconds": t_rt, "draws": draws}

@@ -160,6 +160,8 @@ def sweep_workload(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, out
         out["running_time_fits_bits"] = {str(p): {"c": f.get("running_time_c_bits"), "d": f.get("running_time_d")}
                                          for p, f in res["fits"].items()}
         out["running_time_seconds"] = res["running_time_seconds"]
+        out["draws"] = res["draws"]
+        out["draws_per_s"] = res["draws"] / res["running_time_seconds"] if res["running_time_seconds"] else None
     return out
 
 
@@ -176,6 +178,14 @@ def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p:
         _, ps, nm = api.evolve_batch(n, costs, insts[0].m, g, b, "c128", out=states)
     _sync()
     dt = (time.perf_counter() - t0) / reps
+    # FP64 work of the whole-evolution kernel: per amplitude and layer, n factored
+    # butterfly stages (one FMA per component: 2 FMA per amplitude each) and the
+    # phase multiply (4 FMA-equivalents); 2 flops per FMA.
+    flops = count * (1 << n) * p * (2 * n + 4) * 2
+    fp64_nominal = 1.25e12  # GB300 dense FP64, nominal (not measured here)
     return {"count": count, "n": n, "m": insts[0].m, "p": p, "ms_per_batch": dt * 1e3,
-            "amp_layer_per_s": count * (1 << n) * p / dt, "mean_psucc": float(np.mean(ps)),
+            "amp_layer_per_s": count * (1 << n) * p / dt,
+            "roofline": {"bound": "fp64", "achieved_tflops": flops / dt / 1e12, "peak_tflops": fp64_nominal / 1e12,
+                         "frac": flops / dt / fp64_nominal, "peak_source": "nominal"},
+            "mean_psucc": float(np.mean(ps)),
             "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols))}

@@ -189,3 +189,20 @@ def test_adjoint_schedule_undoes_each_layer_in_reverse(lib, dtype, n, p):
         assert k == n_passes + (p - 1) * (n_passes - 1)
     else:
         assert k == 2 * p
+
+
+def test_sampling_validation_precedes_device_work(lib):
+    """qaoa_sample / qaoa_running_time reject bad arguments on the host."""
+    one = ctypes.c_void_p(1)
+    rt = ctypes.c_int64()
+    assert lib.qaoa_sample(20, one, 0, 0, 16, one, None, None) == _lib_code("EINVAL")          # no output
+    assert lib.qaoa_sample(20, one, 0, 0, 0, one, one, None) == _lib_code("ERANGE")            # k = 0
+    assert lib.qaoa_sample(33, one, 0, 0, 16, one, one, None) == _lib_code("ERANGE")           # n > 32
+    assert lib.qaoa_sample(1, one, 0, 2, 16, one, one, None) == _lib_code("ERANGE")            # halved needs n >= 2
+    assert lib.qaoa_sample(20, one, 5, 0, 16, one, one, None) == _lib_code("EINVAL")           # dtype
+    assert lib.qaoa_sample(20, one, 0, 0x100, 16, one, one, None) == _lib_code("EINVAL")       # unknown flag
+    assert lib.qaoa_sample(20, None, 0, 0, 16, one, one, None) == _lib_code("EINVAL")          # no state
+    assert lib.qaoa_running_time(20, None, one, 0, 0, 16, one, ctypes.byref(rt), None, None) == _lib_code("EINVAL")
+    assert lib.qaoa_running_time(20, one, one, 0, 0, 16, one, None, None, None) == _lib_code("EINVAL")
+    assert lib.qaoa_running_time_batch(0, 20, one, one, 0, 0, 16, one, ctypes.byref(rt), None) == _lib_code("ERANGE")
+    assert lib.qaoa_adjoint_schedule(20, 0, 0, 0, None, None, None) == _lib_code("EINVAL")
