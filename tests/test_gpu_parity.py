@@ -301,3 +301,38 @@ def test_full_size_n30_sampled():
         assert abs(ps64 - ps128) <= C64_PS_TOL * ps128
     del st128
     torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_max_size_n32_sampled():
+    """n = 32, the largest size (m = 256, the sweep's top point): sampled cost
+    entries against the oracle, the clause-count identity over all 2^32 entries,
+    a complex64 evolution (norm, flip symmetry) and the halved state's p_succ
+    against the full one."""
+    n, k, r, p = 32, 5, 8.0, 2
+    inst = gen.raw_instance("full32", n, k, r, 0)
+    assert inst.m == 256
+    cost, sol, mx = api.cost_table(inst)
+    assert mx <= 255  # a count of 256 would need every clause violated at one x
+    xs = gen.rng_for("full32-xs", 0).integers(0, 1 << n, size=20000, dtype=np.uint64)
+    ref = oracle.cost_samples(inst.var, inst.neg, xs)
+    idx = torch.from_numpy(xs.astype(np.int64)).cuda()
+    assert np.array_equal(cost[idx].cpu().numpy(), ref.astype(np.uint8))
+    assert int(cost.sum(dtype=torch.int64).item()) == inst.m * 2 ** (n - k + 1)
+    g, b = gen.linear_ramp(p)
+    st, ps, nm = api.evolve(n, cost, inst.m, g, b, "c64")
+    assert abs(nm - 1) < 1e-5
+    flip = torch.from_numpy(((~xs) & np.uint64((1 << n) - 1)).astype(np.int64)).cuda()
+    assert torch.allclose(st[idx], st[flip], rtol=0, atol=1e-9)
+    del st
+    torch.cuda.empty_cache()
+    from paper_2401_02852_gb300._lib import Z2_HALF
+    half = api.cost_table_half(inst)[0]
+    assert torch.equal(half[:1 << 20], cost[:1 << 20])
+    del cost
+    torch.cuda.empty_cache()
+    _, ps_h, nm_h = api.evolve(n, half, inst.m, g, b, "c64", flags=Z2_HALF)
+    assert abs(nm_h - 1) < 1e-5
+    if sol:
+        assert abs(ps_h - ps) <= C64_PS_TOL * ps
+    torch.cuda.empty_cache()
