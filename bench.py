@@ -360,7 +360,22 @@ def run_native(args, ws, rank, local):
         extra["c128"] = {"ms_per_evolution": ms128, "amp_layer_per_s": (2 ** n) * p / (ms128 / 1000.0),
                          "p_succ": ps128, "c64_rel_err_vs_c128": abs(results["p_succ"] - ps128) / ps128,
                          "c64_speedup_over_c128": ms128 / (ms / args.steps - 0.0)}
-        del st128
+        # the same complex128 evolution in double-float arithmetic (QAOA_DF64)
+        from paper_2401_02852_gb300._lib import DF64
+        std = torch.empty_like(st128)
+        api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=std)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            _, psdf, _ = api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=std)
+        z.record()
+        torch.cuda.synchronize()
+        msdf = a.elapsed_time(z) / reps
+        amp_err = float((std - st128).abs().max().item() / st128.abs().max().item())
+        extra["c128_df64"] = {"ms_per_evolution": msdf, "amp_layer_per_s": (2 ** n) * p / (msdf / 1000.0),
+                              "p_succ": psdf, "p_succ_rel_diff_vs_fp64": abs(psdf - ps128) / ps128,
+                              "max_amp_diff_vs_fp64_over_max_amp": amp_err, "speedup_over_fp64": ms128 / msdf}
+        del st128, std
 
     if args.serve_requests > 0 and rank == 0 and ws == 1:
         from paper_2401_02852_gb300 import workloads

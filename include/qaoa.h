@@ -72,6 +72,15 @@ extern "C" {
  * full state.  Exact: the same numbers as the full evolution, half the bytes. */
 #define QAOA_Z2_HALF 0x2
 
+/* QAOA_DF64 (complex128 evolutions only, full state, not for the gradient):
+ * the state stays complex128 in memory and in the result, but between passes
+ * it is held as double-float pairs (hi + lo floats, about 48 significant bits)
+ * and the butterflies and phases run in that arithmetic on the FP32 pipes,
+ * which on GB300 are far faster than the FP64 pipe.  Per-operation error about
+ * 2^-46 of the operands instead of 2^-53.  Small n (the one-CTA path) runs in
+ * FP64 regardless. */
+#define QAOA_DF64 0x4
+
 #define QAOA_MAX_N 32
 #define QAOA_MAX_M 1023
 

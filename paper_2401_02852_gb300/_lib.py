@@ -19,6 +19,7 @@ ERRORS = {-1: "EINVAL", -2: "ERANGE", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
 C64, C128 = 0, 1
 MIXER_PAPER, MIXER_RX2B = 0, 1
 Z2_HALF = 2
+DF64 = 4
 
 
 class QaoaError(RuntimeError):

@@ -526,6 +526,8 @@ static int grad_common(int batch, int n, const uint8_t *cost, int m, int p, cons
                        void *stream_) {
     if (batch < 1) return set_error(QAOA_EINVAL, "batch=%d", batch);
     if (dtype != QAOA_C64 && dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", dtype);
+    if (flags & ~QAOA_MIXER_RX2B)
+        return set_error(QAOA_EINVAL, "flags=0x%x: the gradient takes the full state in native arithmetic", flags);
     const int nmax = dtype == QAOA_C64 ? QAOA_MAX_N : QAOA_MAX_N - 1;
     if (n < 1 || n > nmax) return set_error(QAOA_ERANGE, "n=%d outside [1, %d]", n, nmax);
     if (m < 0 || m > QAOA_MAX_M) return set_error(QAOA_ERANGE, "m=%d", m);

@@ -14,7 +14,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "pass_common.cuh"
@@ -115,11 +117,34 @@ __host__ __device__ __forceinline__ constexpr uint32_t land(uint32_t u) {
 // run downwards.  Indices inside one instance fit in 32 bits (n <= 32).
 // sc: the tile's cost bytes in shared memory, indexed by tile element (by
 // landing position when Z2).
+// |v|^2 and a zero amplitude for each arithmetic (double-float: in FP64).
+__device__ __forceinline__ float amp_prob(const float2 &v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ double amp_prob(const double2 &v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ double amp_prob(const float4 &v) {
+    const double re = (double)v.x + (double)v.y, im = (double)v.z + (double)v.w;
+    return re * re + im * im;
+}
+template <typename V>
+__device__ __forceinline__ V zero_amp() {
+    V z;
+    memset(&z, 0, sizeof z);
+    return z;
+}
+
+// A double-float evolution keeps its state as (re.hi, re.lo, im.hi, im.lo)
+// floats in the complex128 buffer; its last pass (always a reducing one)
+// writes FP64 (re, im) back, 16 bytes for 16 bytes.
+template <typename R>
+constexpr bool is_df() {
+    return std::is_same<R, dfloat>::value;
+}
+
 template <typename R, int LO, int ROW, bool Z2, bool RED>
 __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename Cx<R>::V *sp, const uint8_t *sc,
                                            typename Cx<R>::V *sa, uint32_t gstride, bool mirror, bool reduce,
                                            double acc[2]) {
     using V = typename Cx<R>::V;
+    using P = decltype(amp_prob(v[0]));  // probability accumulation type
     constexpr int NR = Cx<R>::NR;
     // Opaque to the compiler: otherwise it keeps the load phase's 32 offsets
     // live across the whole tile to reuse them here.
@@ -129,24 +154,28 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
         const uint32_t o = (u & ((1u << ROW) - 1u)) + (u >> ROW) * gstride;
         return (Z2 && mirror) ? -(int64_t)o : (int64_t)o;
     };
+    if (is_df<R>() && RED && reduce) {  // the evolution's last pass: FP64 out
+        double2 *sd = reinterpret_cast<double2 *>(sp);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) sp[off(r)] = v[r];
+        for (int r = 0; r < NR; ++r) {
+            const float4 w = *reinterpret_cast<const float4 *>(&v[r]);
+            sd[off(r)] = make_double2((double)w.x + (double)w.y, (double)w.z + (double)w.w);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sp[off(r)] = v[r];
+    }
     if (RED && reduce) {
-        R ps = 0, nm = 0;
+        P ps = 0, nm = 0;
         const uint32_t tid = threadIdx.x;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const R w = v[r].x * v[r].x + v[r].y * v[r].y;
+            const P w = amp_prob(v[r]);
             nm += w;
             const uint32_t u = tile_elem<Cx<R>, LO>(tid, r);
             const bool sol = sc[Z2 ? land<Cx<R>::T>(u) : u] == 0;
             if (sol) ps += w;
-            if (sa) {
-                V z;
-                z.x = sol ? v[r].x : R(0);
-                z.y = sol ? v[r].y : R(0);
-                sa[off(r)] = z;
-            }
+            if (sa) sa[off(r)] = sol ? v[r] : zero_amp<V>();
         }
         acc[0] += (double)ps;
         acc[1] += (double)nm;
@@ -325,11 +354,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constan
     uint8_t *scs = reinterpret_cast<uint8_t *>(tile + Cx<R>::TILE_ELEMS);
     V *stab = reinterpret_cast<V *>(scs + (2 << T));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
-        for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) {
-            V z;
-            z.x = z.y = 0;
-            stab[i] = i <= a.m ? tab.t[i] : z;
-        }
+        for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) stab[i] = i <= a.m ? tab.t[i] : zero_amp<V>();
         __syncthreads();
     }
     pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW, FULL>(a, stab, tile, scs);
@@ -576,6 +601,13 @@ struct LowSet {
     }
 };
 
+// Stand-in for the halved-state kernels where an arithmetic has none
+// (double-float evolutions take the full state only).
+template <typename R>
+struct NoLowSet {
+    void all(std::vector<KPtr> &) const {}
+};
+
 template <typename R>
 struct PassKernels {
     using Full = PhaseTab<R, MAX_TABLE>;
@@ -584,7 +616,7 @@ struct PassKernels {
     // complex128 has no wide rows and those are the narrow kernels again
     static constexpr int WROW = sizeof(R) == 4 ? HIGH_ROW + 1 : HIGH_ROW;
     LowSet<R, false> low;
-    LowSet<R, true> low_z2;
+    typename std::conditional<is_df<R>(), NoLowSet<R>, LowSet<R, true>>::type low_z2;
     HighSet<R, HIGH_ROW, true> high;     // [wide][full] below
     HighSet<R, HIGH_ROW, false> high_part;
     HighSet<R, WROW, true> wide;
@@ -637,6 +669,24 @@ int pass_grid_x(int dtype, int n, int batch) {
     return grid_x(di.sms, 2, batch, 1ull << (n - T));  // two persistent CTAs per SM
 }
 
+// Host conversions of FP64 values to each arithmetic (double-float: the
+// nearest float, then the nearest float to the remainder).
+template <typename R>
+static R real_from(double x) {
+    return (R)x;
+}
+template <>
+dfloat real_from<dfloat>(double x) {
+    const float hi = (float)x;
+    return dfloat{hi, (float)(x - (double)hi)};
+}
+static float2 amp_from(float2 *, double re, double im) { return make_float2((float)re, (float)im); }
+static double2 amp_from(double2 *, double re, double im) { return make_double2(re, im); }
+static float4 amp_from(float4 *, double re, double im) {
+    const dfloat r = real_from<dfloat>(re), i = real_from<dfloat>(im);
+    return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+
 template <typename R>
 static void fill_table(typename PassKernels<R>::Full *tab, const EvolveReq &r, int l, int sign) {
     std::vector<double> re(r.m + 1), im(r.m + 1);
@@ -644,10 +694,7 @@ static void fill_table(typename PassKernels<R>::Full *tab, const EvolveReq &r, i
     double scale = std::pow(k.sigma, r.n);
     if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
     phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());
-    for (int c = 0; c <= r.m; ++c) {
-        tab->t[c].x = (R)re[c];
-        tab->t[c].y = (R)im[c];
-    }
+    for (int c = 0; c <= r.m; ++c) tab->t[c] = amp_from(&tab->t[c], re[c], im[c]);
 }
 
 template <typename R>
@@ -691,21 +738,22 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
             a.active = ((1u << ps.bits) - 1u) << (T - ps.bits);
         }
         const bool last = i + 1 == seq.size();
-        a.reduce = (last && (want || r.adj)) ? 1 : 0;
+        // a double-float evolution's last pass always reduces: it writes FP64 out
+        a.reduce = (last && (want || r.adj || is_df<R>())) ? 1 : 0;
         if (a.reduce && !(L.mode == MODE_PLAIN || (L.mode == MODE_INIT && low)))
             return set_error(QAOA_ECUDA, "schedule: the last pass has mode %d", L.mode);
         a.adj = (last && r.adj) ? reinterpret_cast<V *>(r.adj) : nullptr;
         const LayerCoef k1 = r.p > 0 ? layer_coef(r.beta[L.la], sign) : LayerCoef{1.0, 1.0, 0.0, true};
         a.ua1 = k1.unit_a;
-        a.A1 = (R)k1.A;
-        a.B1 = (R)k1.B;
+        a.A1 = real_from<R>(k1.A);
+        a.B1 = real_from<R>(k1.B);
         a.ua2 = 1;
-        a.A2 = a.B2 = (R)0;
+        a.A2 = a.B2 = real_from<R>(0.0);
         if (L.mode == MODE_FUSED) {
             const LayerCoef k2 = layer_coef(r.beta[L.la + 1], sign);
             a.ua2 = k2.unit_a;
-            a.A2 = (R)k2.A;
-            a.B2 = (R)k2.B;
+            a.A2 = real_from<R>(k2.A);
+            a.B2 = real_from<R>(k2.B);
         }
         a.tiles = 1ull << (pl.state_bits - T);
         const int kind = low ? K_PASS_LOW : K_PASS_HIGH;
@@ -713,21 +761,27 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         const int u1 = a.ua1 ? 1 : 0, u2 = a.ua2 ? 1 : 0;
         const size_t smem_phase = pass_smem<R>(true, r.m), smem_plain = pass_smem<R>(false, 0);
         if (low) {
-            const LowSet<R, false> &ls = pk->low;
-            const LowSet<R, true> &lz = pk->low_z2;
-            if (L.mode == MODE_INIT) {
-                fill_table<R>(tab, r, 0, sign);
-                auto k = r.p == 0 ? (z2 ? lz.init0 : ls.init0) : (z2 ? lz.init[u1] : ls.init[u1]);
-                k<<<grid, block, smem_phase, stream>>>(a, *tab);
-            } else if (L.mode == MODE_PHASE) {
-                fill_table<R>(tab, r, L.la, sign);
-                (z2 ? lz.phase[u1] : ls.phase[u1])<<<grid, block, smem_phase, stream>>>(a, *tab);
-            } else if (L.mode == MODE_PLAIN) {
-                auto k = a.reduce ? (z2 ? lz.plain_red[u1] : ls.plain_red[u1]) : (z2 ? lz.plain[u1] : ls.plain[u1]);
-                k<<<grid, block, smem_plain, stream>>>(a, none);
-            } else {
-                return set_error(QAOA_ECUDA, "schedule: fused low pass");
-            }
+            // the full-state or the halved-state set (double-float has only the former)
+            auto launch_low = [&](const auto &ls) -> int {
+                if (L.mode == MODE_INIT) {
+                    fill_table<R>(tab, r, 0, sign);
+                    (r.p == 0 ? ls.init0 : ls.init[u1])<<<grid, block, smem_phase, stream>>>(a, *tab);
+                } else if (L.mode == MODE_PHASE) {
+                    fill_table<R>(tab, r, L.la, sign);
+                    ls.phase[u1]<<<grid, block, smem_phase, stream>>>(a, *tab);
+                } else if (L.mode == MODE_PLAIN) {
+                    (a.reduce ? ls.plain_red[u1] : ls.plain[u1])<<<grid, block, smem_plain, stream>>>(a, none);
+                } else {
+                    return set_error(QAOA_ECUDA, "schedule: fused low pass");
+                }
+                return QAOA_OK;
+            };
+            int lrc = QAOA_OK;
+            if constexpr (is_df<R>())
+                lrc = z2 ? set_error(QAOA_EINVAL, "double-float takes the full state") : launch_low(pk->low);
+            else
+                lrc = z2 ? launch_low(pk->low_z2) : launch_low(pk->low);
+            if (lrc) return lrc;
         } else {
             // rows of HIGH_ROW or WROW bits; FULL kernels when no bit of the group is a carried one
             const bool wide = ps.row != HIGH_ROW, full = ps.bits == T - ps.row;
@@ -829,6 +883,7 @@ static int validate_evolve(int batch, int n, const uint8_t *cost, int m, int p, 
 
 int evolve_device_impl(const EvolveReq &r, cudaStream_t stream, double *d_partials, int gx) {
     if (r.dtype == QAOA_C64) return evolve_passes<float>(r, d_partials, gx, stream);
+    if (r.flags & QAOA_DF64) return evolve_passes<dfloat>(r, d_partials, gx, stream);
     return evolve_passes<double>(r, d_partials, gx, stream);
 }
 
@@ -843,6 +898,8 @@ static int evolve_common(int batch, int n, const uint8_t *d_cost, int m, int p, 
     int rc = validate_evolve(batch, n, d_cost, m, p, gamma, beta, dtype, d_state);
     if (rc) return rc;
     const bool z2 = (flags & QAOA_Z2_HALF) != 0;
+    if ((flags & QAOA_DF64) && (dtype != QAOA_C128 || z2 || adj))
+        return set_error(QAOA_EINVAL, "QAOA_DF64 takes a complex128 full-state evolution (no halved state, no gradient)");
     if (z2 && n <= small_n_limit(dtype))
         return set_error(QAOA_ERANGE, "halved state needs n > %d (n=%d)", small_n_limit(dtype), n);
     if (z2 && adj) return set_error(QAOA_EINVAL, "the gradient does not take the halved state");

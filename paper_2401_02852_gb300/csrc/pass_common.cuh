@@ -28,6 +28,33 @@ constexpr int PT = 256;  // threads per pass CTA (8 thread bits)
 // Row width (bits) of every high-pass tile: 16 contiguous amplitudes.
 constexpr int HIGH_ROW = 4;
 
+// Double-float number: the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits (Dekker 1971; the arithmetic
+// below is Knuth's TwoSum, Dekker's Fast2Sum and the FMA form of Dekker's
+// TwoProduct).  On GB300 the FP32 pipes are 64 times as fast as the FP64 pipe,
+// so complex128 evolutions can run their butterflies and phases in this
+// arithmetic (QAOA_DF64) and stay accurate to about 1e-14 per operation.
+struct dfloat {
+    float hi, lo;
+};
+
+// Register/shared-memory amplitude of each arithmetic: (re, im), or for
+// double-float (re.hi, re.lo, im.hi, im.lo).
+template <typename R>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    using type = float2;
+};
+template <>
+struct VecOf<double> {
+    using type = double2;
+};
+template <>
+struct VecOf<dfloat> {
+    using type = float4;
+};
+
 // Tile geometry: element type R, 2^T amplitudes per tile, 2^RB per thread,
 // 2^(T - RB) threads.  The load mapping (LO = T - RB) puts the registers on the
 // top RB tile bits, so lanes run along tile bits 0..4 (coalesced, and dense in
@@ -36,7 +63,7 @@ constexpr int HIGH_ROW = 4;
 // mapping used).
 template <typename R, int T_, int RB_>
 struct Geo {
-    using V = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    using V = typename VecOf<R>::type;
     using Real = R;
     static constexpr int T = T_;
     static constexpr int RB = RB_;
@@ -67,6 +94,10 @@ template <>
 struct FwdGeoT<double> {
     using type = Geo<double, 12, 4>;
 };
+template <>
+struct FwdGeoT<dfloat> {  // complex128 storage, double-float arithmetic: 16 B per amplitude
+    using type = Geo<dfloat, 12, 4>;
+};
 template <typename R>
 using Cx = typename FwdGeoT<R>::type;
 
@@ -81,34 +112,37 @@ struct Round {
 // The rounds of the low pass (all T tile bits) and of a high pass (tile bits
 // [4, T): rows of 16 contiguous amplitudes), per forward geometry.  The first
 // round is the load mapping; the last round's mapping is also coalesced.
-template <typename G, bool LOW>
-struct PassRounds;
+template <int T, int RB, bool LOW>
+struct RoundsFor;
 template <>
-struct PassRounds<Geo<float, 13, 5>, true> {
+struct RoundsFor<13, 5, true> {
     static constexpr int N = 3, LAST = 5;
     using R0 = Round<8, 0x1F00>;
     using R1 = Round<0, 0x001F>;
     using R2 = Round<5, 0x00E0>;
 };
 template <>
-struct PassRounds<Geo<float, 13, 5>, false> {
+struct RoundsFor<13, 5, false> {
     static constexpr int N = 2, LAST = 4;
     using R0 = Round<8, 0x1F00>;
     using R1 = Round<4, 0x00F0>;
 };
 template <>
-struct PassRounds<Geo<double, 12, 4>, true> {
+struct RoundsFor<12, 4, true> {
     static constexpr int N = 3, LAST = 4;
     using R0 = Round<8, 0xF00>;
     using R1 = Round<0, 0x00F>;
     using R2 = Round<4, 0x0F0>;
 };
 template <>
-struct PassRounds<Geo<double, 12, 4>, false> {
+struct RoundsFor<12, 4, false> {
     static constexpr int N = 2, LAST = 4;
     using R0 = Round<8, 0xF00>;
     using R1 = Round<4, 0x0F0>;
 };
+// The rounds depend only on the tile shape (T, RB), not on the arithmetic.
+template <typename G, bool LOW>
+struct PassRounds : RoundsFor<G::T, G::RB, LOW> {};
 
 template <typename G, int LO>
 __device__ __forceinline__ uint32_t tile_elem(uint32_t tid, uint32_t r) {
@@ -141,6 +175,42 @@ __device__ __forceinline__ V cmul(V a, V b) {
     return r;
 }
 
+// ---- double-float arithmetic (no contraction: every step rounds once) -------
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float &s, float &e) {  // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// x + c y for double-floats (the lo x lo product is below the format's
+// precision and dropped).
+__device__ __forceinline__ dfloat df_axpy(dfloat c, float y_hi, float y_lo, float x_hi, float x_lo) {
+    const float p = __fmul_rn(c.hi, y_hi);
+    const float pe = __fmaf_rn(c.hi, y_hi, -p);  // c.hi y.hi = p + pe exactly
+    float s, se;
+    df_two_sum(x_hi, p, s, se);
+    float lo = __fadd_rn(__fadd_rn(se, pe), x_lo);
+    lo = __fmaf_rn(c.hi, y_lo, lo);
+    lo = __fmaf_rn(c.lo, y_hi, lo);
+    dfloat r;
+    df_fast_two_sum(s, lo, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ dfloat df_neg(dfloat c) { return dfloat{-c.hi, -c.lo}; }
+
+// Complex product in double-float: (a.re b.re - a.im b.im, a.re b.im + a.im b.re).
+__device__ __forceinline__ float4 cmul(float4 a, float4 b) {
+    const dfloat are{a.x, a.y}, aim{a.z, a.w};
+    const dfloat t = df_axpy(are, b.x, b.y, 0.f, 0.f);
+    const dfloat re = df_axpy(df_neg(aim), b.z, b.w, t.hi, t.lo);
+    const dfloat u = df_axpy(are, b.z, b.w, 0.f, 0.f);
+    const dfloat im = df_axpy(aim, b.x, b.y, u.hi, u.lo);
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
 // Mixer butterfly in factored form: (a, b) <- (A a + i B b, i B a + A b) with
 // A = 1 (UA) or B = 1; the dropped scalar sigma^n is folded into the phase table.
 template <bool UA, typename V, typename R>
@@ -156,6 +226,34 @@ __device__ __forceinline__ void bfly(V &a, V &b, R A, R B) {
         na.y = fma(A, a.y, b.x);
         nb.x = fma(A, b.x, -a.y);
         nb.y = fma(A, b.y, a.x);
+    }
+    a = na;
+    b = nb;
+}
+
+// The factored butterfly in double-float arithmetic (float4 amplitudes).
+template <bool UA>
+__device__ __forceinline__ void bfly(float4 &a, float4 &b, dfloat A, dfloat B) {
+    float4 na, nb;
+    if (UA) {  // (a + i B b, b + i B a)
+        const dfloat nB = df_neg(B);
+        dfloat t = df_axpy(nB, b.z, b.w, a.x, a.y);
+        na.x = t.hi, na.y = t.lo;
+        t = df_axpy(B, b.x, b.y, a.z, a.w);
+        na.z = t.hi, na.w = t.lo;
+        t = df_axpy(nB, a.z, a.w, b.x, b.y);
+        nb.x = t.hi, nb.y = t.lo;
+        t = df_axpy(B, a.x, a.y, b.z, b.w);
+        nb.z = t.hi, nb.w = t.lo;
+    } else {  // (A a + i b, A b + i a)
+        dfloat t = df_axpy(A, a.x, a.y, -b.z, -b.w);
+        na.x = t.hi, na.y = t.lo;
+        t = df_axpy(A, a.z, a.w, b.x, b.y);
+        na.z = t.hi, na.w = t.lo;
+        t = df_axpy(A, b.x, b.y, -a.z, -a.w);
+        nb.x = t.hi, nb.y = t.lo;
+        t = df_axpy(A, b.z, b.w, a.x, a.y);
+        nb.z = t.hi, nb.w = t.lo;
     }
     a = na;
     b = nb;
