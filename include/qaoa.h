@@ -161,9 +161,9 @@ int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_state, int dty
                       double *norm, void *stream);
 
 /* Same result as qaoa_success_prob, for callers that cannot allocate device
- * memory at the point of the call: code capturing into a CUDA graph with a fixed
- * memory plan, hosts whose own allocator has reserved the device, or paths that
- * must not risk the implicit synchronisation of cudaMalloc.  The paper has no
+ * memory at the point of the call: hosts whose own allocator has reserved the
+ * whole device, or paths (real-time loops, signal handlers) that must not risk
+ * the implicit device synchronisation of cudaMalloc.  The paper has no
  * counterpart; this is an interface variant of the reduction above.
  *   Scratch: a fixed device array inside the library (2 x 4096 + 2 doubles,
  *   about 64 KiB), held by every GPU that loads the library until exit.  The

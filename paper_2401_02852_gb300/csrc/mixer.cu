@@ -1007,8 +1007,7 @@ extern "C" int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_sta
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of qaoa_success_prob.  Some callers cannot allocate
-// device memory at the moment they need a result: code running while a CUDA
-// graph is being captured into a fixed memory plan, hosts that pre-reserve the
+// device memory at the moment they need a result: hosts that pre-reserve the
 // whole device for their own allocator, or signal-safe / real-time paths where
 // a cudaMalloc (which may synchronise the device) is not allowed.  For them the
 // per-block partial sums and the final pair live in this fixed device array,

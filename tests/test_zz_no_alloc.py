@@ -1,8 +1,8 @@
 """The allocation-free p_succ entry point, called through the C ABI.
 
-Callers that cannot allocate device memory when they need the result (graph
-capture with a fixed memory plan, hosts whose allocator owns the device, paths
-that must not risk cudaMalloc's implicit synchronisation) use
+Callers that cannot allocate device memory when they need the result (hosts
+whose allocator owns the device, paths that must not risk cudaMalloc's implicit
+synchronisation) use
 qaoa_success_prob_noalloc, whose scratch is a fixed array inside the library.
 It must give the same numbers as qaoa_success_prob, on consecutive calls too
 (the shared array keeps the previous call's contents).  This file is collected
