@@ -82,6 +82,32 @@ __device__ __forceinline__ void inv_round(typename G::V *vp, typename G::V *vl, 
     }
 }
 
+// Mapping change of both states.  complex64 amplitudes of psi and lam are
+// packed into one 16-byte element per tile position and moved in one exchange
+// over both buffers (half the shared-memory instructions and barriers of two
+// 8-byte exchanges; the 16-byte padded layout is the complex128 one, conflict
+// free for the same mappings); complex128 states are exchanged one by one.
+template <typename G, int FROM, int TO>
+__device__ __forceinline__ void exchange_pair(typename G::V *vp, typename G::V *vl, typename G::V *tp,
+                                              typename G::V *tl) {
+    if constexpr (sizeof(typename G::V) == 8) {
+        using G4 = Geo<dfloat, G::T, G::RB>;  // 16-byte elements, same tile shape
+        static_assert(G4::TILE_ELEMS == G::TILE_ELEMS, "tile shapes differ");
+        float4 w[G::NR];
+#pragma unroll
+        for (int r = 0; r < G::NR; ++r) w[r] = make_float4(vp[r].x, vp[r].y, vl[r].x, vl[r].y);
+        exchange<G4, FROM, TO>(w, reinterpret_cast<float4 *>(tp));  // tp and tl are adjacent
+#pragma unroll
+        for (int r = 0; r < G::NR; ++r) {
+            vp[r] = make_float2(w[r].x, w[r].y);
+            vl[r] = make_float2(w[r].z, w[r].w);
+        }
+    } else {
+        exchange<G, FROM, TO>(vp, tp);
+        exchange<G, FROM, TO>(vl, tl);
+    }
+}
+
 // State offset of register r's tile element in mapping LO: its row part plus
 // its group part times gstride = 2^lo (ROW: the tile's contiguous bits).
 template <int LO, int ROW>
@@ -178,27 +204,22 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
         };
         inv_round<G, LD, T>(vp, vl, active, a.c, a.S, term);
         if (LOW) {
-            exchange<G, LD, 0>(vp, tp);
-            exchange<G, LD, 0>(vl, tl);
+            exchange_pair<G, LD, 0>(vp, vl, tp, tl);
             inv_round<G, 0, T>(vp, vl, active, a.c, a.S, term);
-            exchange<G, 0, LC>(vp, tp);
-            exchange<G, 0, LC>(vl, tl);
+            exchange_pair<G, 0, LC>(vp, vl, tp, tl);
             prefetch();
             inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
             if (PH) undo_phase();
         } else if (MODE == A_FUSED) {
-            exchange<G, LD, LC>(vp, tp);
-            exchange<G, LD, LC>(vl, tl);
+            exchange_pair<G, LD, LC>(vp, vl, tp, tl);
             inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
             undo_phase();
             inv_round<G, LC, LD>(vp, vl, active, a.c2, a.S2, term2);
-            exchange<G, LC, LD>(vp, tp);
-            exchange<G, LC, LD>(vl, tl);
+            exchange_pair<G, LC, LD>(vp, vl, tp, tl);
             prefetch();
             inv_round<G, LD, T>(vp, vl, active, a.c2, a.S2, term2);
         } else {
-            exchange<G, LD, LC>(vp, tp);
-            exchange<G, LD, LC>(vl, tl);
+            exchange_pair<G, LD, LC>(vp, vl, tp, tl);
             prefetch();
             inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
         }
