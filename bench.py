@@ -415,6 +415,10 @@ def run_workload(args):
     elif args.workload == "sweep":
         res = workloads.sweep_workload(ns=range(args.sweep_n0, args.sweep_n1 + 1, 2), seeds=args.seeds,
                                        out_dir=args.out_dir)
+    elif args.workload == "protocol":
+        res = workloads.protocol_workload(ks=tuple(int(k) for k in args.ks.split(",")),
+                                          ps=tuple(int(p) for p in args.ps.split(",")),
+                                          count=args.count, lr=args.lr)
     else:
         res = workloads.batch_workload()
     res["workload"] = args.workload
@@ -438,7 +442,7 @@ def main():
     ap.add_argument("--no-z2", dest="z2", action="store_false", help="skip the halved-state measurement")
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="short serving run (Poisson 200/s) reported beside the headline; 0 skips it")
-    ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch"], default="evolve")
+    ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch", "protocol"], default="evolve")
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--batch", type=int, default=256)
@@ -449,6 +453,10 @@ def main():
     ap.add_argument("--sweep-n1", type=int, default=32)
     ap.add_argument("--seeds", type=int, default=200)
     ap.add_argument("--out-dir", default=None)
+    ap.add_argument("--ks", default="9", help="protocol: clause widths (comma separated)")
+    ap.add_argument("--ps", default="1,2,4,8,16,32", help="protocol: depths (comma separated)")
+    ap.add_argument("--count", type=int, default=2500, help="protocol: satisfiable instances per (k, n)")
+    ap.add_argument("--lr", type=float, default=1e-3, help="protocol: Adam learning rate of the angle training")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -43,7 +43,7 @@ extern "C" {
 #define QAOA_OK 0
 #define QAOA_PENDING 1     /* serving: request not finished yet                */
 #define QAOA_EINVAL (-1)   /* malformed argument (NULL, bad enum, bad clause)   */
-#define QAOA_ERANGE (-2)   /* size out of range (n > 32, m > 1023, k > n,
+#define QAOA_ERANGE (-2)   /* size out of range (n > 32, m > 8191, k > n,
                               max C > 255 for the uint8 table, tile limits)     */
 #define QAOA_ENOMEM (-3)   /* device or host allocation failed / over budget    */
 #define QAOA_ECUDA (-4)    /* a CUDA runtime call failed (message has details)  */
@@ -82,7 +82,10 @@ extern "C" {
 #define QAOA_DF64 0x4
 
 #define QAOA_MAX_N 32
-#define QAOA_MAX_M 1023
+/* Clause counts up to 8191 cover the threshold densities of k = 3..10 at the
+ * paper's sizes (Sec. "Random Problems": m ~ Poisson(r n), r near the
+ * satisfiability threshold, about 350 n at k = 10). */
+#define QAOA_MAX_M 8191
 
 /* One NAE-k-SAT instance, host memory.  var[i*k + j] in [0, n) is the variable
  * of literal j of clause i (distinct within a clause); neg[i*k + j] in {0, 1}
@@ -106,7 +109,7 @@ int qaoa_release_scratch(void);
 /* ---- cost table (Eq. for C^NAE, Sec. "Problem Hamiltonian") ----------------
  * C(x) = number of clauses whose k literals are all false or all true
  * (De Morgan form, Appendix A.2), for every x in [0, 2^n).
- *   inst      host instance (validated: 1 <= n <= 32, 0 <= m <= 1023,
+ *   inst      host instance (validated: 1 <= n <= 32, 0 <= m <= 8191,
  *             1 <= k <= n, variables distinct within a clause).
  *   d_cost    device uint8 [2^n], written.
  *   n_sol     host, nullable: number of x with C(x) = 0 (exact brute force).
@@ -134,7 +137,8 @@ int naesat_cost_table_batch(int batch, const naesat_instance *insts, uint8_t *d_
  * U_C(gamma) = diag(exp(-i gamma C(x))) (Eq. for U_C) and the mixer of `flags`.
  *   n        1..32 (C64) / 1..31 (C128); the state must fit in device memory.
  *   d_cost   device uint8 [2^n] from naesat_cost_table.
- *   m        number of clauses (bounds C; phase tables have m + 1 entries).
+ *   m        number of clauses, 0 <= m <= 8191 (bounds C; the phase tables
+ *            have min(m, 255) + 1 entries, the uint8 costs index no more).
  *   p        depth >= 0 (p = 0 returns |+>^n).
  *   gamma, beta  host float64 [p].
  *   dtype    QAOA_C64 or QAOA_C128.

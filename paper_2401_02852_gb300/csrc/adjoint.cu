@@ -378,14 +378,14 @@ static int adj_init(AdjKernels<R> **out) {
                                              (int)adj_smem<R>(-1));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(ks.low_phase, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)adj_smem<R>(QAOA_MAX_M));
+                                     (int)adj_smem<R>(MAX_TABLE - 1));
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
             for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
                 e = cudaFuncSetAttribute(ks.high[w][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)adj_smem<R>(-1));
                 if (e == cudaSuccess)
                     e = cudaFuncSetAttribute(ks.fused[w][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)adj_smem<R>(QAOA_MAX_M));
+                                             (int)adj_smem<R>(MAX_TABLE - 1));
             }
         const int small = (int)(2 * sizeof(typename Cx<R>::V) * (size_t(1) << Cx<R>::T) + (size_t(1) << Cx<R>::T));
         if (e == cudaSuccess)
@@ -556,6 +556,7 @@ static int grad_common(int batch, int n, const uint8_t *cost, int m, int p, cons
     if (!cost || !state || !adj || !gamma || !beta || !dgamma || !dbeta) return set_error(QAOA_EINVAL, "NULL argument");
     for (int l = 0; l < p; ++l)
         if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l])) return set_error(QAOA_EINVAL, "angle %d not finite", l);
+    m = table_top(m);  // from here m bounds the phase tables only
     cudaStream_t stream = (cudaStream_t)stream_;
     Scratch *sc = nullptr;
     int rc;

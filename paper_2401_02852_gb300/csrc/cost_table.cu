@@ -18,6 +18,12 @@
 // counts two words per record load.  The number of
 // solutions (count 0) and the largest count come out of the same pass.
 //
+// Large clause counts.  The records are staged CT_CHUNK at a time: the block
+// filters and counts one chunk, then the next, accumulating into the same
+// counters.  Up to 1023 clauses 10 bit planes count exactly; beyond that 13
+// planes do (m <= 8191).  Only the counts <= 255 go into the table; a larger
+// one makes the call fail with the exact maximum.
+//
 // Clause filtering.  A block takes 512 consecutive words at a time, so the
 // variables >= 14 (SUB_BITS) are constant over them.  A clause whose literals
 // on those variables are neither all true nor all false is violated nowhere in
@@ -35,10 +41,15 @@
 namespace qaoa {
 
 constexpr int CT_THREADS = 256;
+constexpr int CT_CHUNK = 1024;     // clause records staged in shared memory at a time
+constexpr int CT_PARAM_M = 1023;   // largest m passed as kernel parameters
+constexpr int NPL_SMALL = 10;      // bit planes for m <= 1023
+constexpr int NPL_LARGE = 13;      // bit planes for m <= 8191
+static_assert(QAOA_MAX_M < (1 << NPL_LARGE), "counts must fit the planes");
 
 struct CostParams {
     int n, m;
-    ClauseRec rec[QAOA_MAX_M];
+    ClauseRec rec[CT_PARAM_M];
 };
 
 __device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
@@ -53,10 +64,11 @@ __device__ __forceinline__ uint32_t violation_word(uint32_t xh, const ClauseRec 
 }
 
 // Carry-save counter of the violated clauses of one 32-assignment word:
-// bit plane q holds bit q of every count (q = 0..9, counts up to 1023).
+// bit plane q holds bit q of every count (q = 0..NPL-1, counts < 2^NPL).
+template <int NPL>
 struct WordCounter {
     uint32_t ones = 0, twos = 0, fours = 0, eights = 0;
-    uint32_t up[6] = {0, 0, 0, 0, 0, 0};
+    uint32_t up[NPL - 4] = {};
     // Adds 16 violation words (a Harley-Seal chunk).
     __device__ __forceinline__ void add16(const uint32_t v[16]) {
         uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
@@ -77,29 +89,30 @@ struct WordCounter {
         csa(sixteens, eights, eights, eightsA, eightsB);
         uint32_t carry = sixteens;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
+        for (int q = 0; q < NPL - 4; ++q) {
             const uint32_t t = up[q] & carry;
             up[q] ^= carry;
             carry = t;
         }
     }
-    __device__ __forceinline__ void planes(uint32_t p[10]) const {
+    __device__ __forceinline__ void planes(uint32_t p[NPL]) const {
         p[0] = ones;
         p[1] = twos;
         p[2] = fours;
         p[3] = eights;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) p[4 + q] = up[q];
+        for (int q = 0; q < NPL - 4; ++q) p[4 + q] = up[q];
     }
 };
 
-// Counts two words X0, X1 against the clause records in shared memory
-// (m16 = m rounded up to 16; the padding records are all zero, which are never
-// violated: t = 0 = hi_mask selects all_false | all_true = 0).
-__device__ __forceinline__ void count_words2(uint32_t X0, uint32_t X1, int m16, const uint4 *srec, uint32_t p0[10],
-                                             uint32_t p1[10]) {
+// Adds to c0, c1 the counts of words X0, X1 against the clause records in
+// shared memory (m16 = record count rounded up to 16; the padding records are
+// all zero, which are never violated: t = 0 = hi_mask selects
+// all_false | all_true = 0).
+template <int NPL>
+__device__ __forceinline__ void count_words2(uint32_t X0, uint32_t X1, int m16, const uint4 *srec,
+                                             WordCounter<NPL> &c0, WordCounter<NPL> &c1) {
     const uint32_t xh0 = X0 << 5, xh1 = X1 << 5;
-    WordCounter c0, c1;
     for (int i0 = 0; i0 < m16; i0 += 16) {
         uint32_t v0[16], v1[16];
 #pragma unroll
@@ -112,8 +125,6 @@ __device__ __forceinline__ void count_words2(uint32_t X0, uint32_t X1, int m16, 
         c0.add16(v0);
         c1.add16(v1);
     }
-    c0.planes(p0);
-    c1.planes(p1);
 }
 
 // 8x8 bit transpose of a 64-bit word (byte j = row j, bit i = column i).
@@ -129,7 +140,7 @@ __device__ __forceinline__ uint64_t transpose8(uint64_t w) {
 }
 
 // Byte b of the result (b = 0..31) = bits 0..7 of the count of x = 32 X + b.
-__device__ __forceinline__ void planes_to_bytes(const uint32_t planes[10], uint32_t out[8]) {
+__device__ __forceinline__ void planes_to_bytes(const uint32_t *planes, uint32_t out[8]) {
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         // row j of the 8x8 block = byte g of plane j
@@ -144,16 +155,21 @@ __device__ __forceinline__ void planes_to_bytes(const uint32_t planes[10], uint3
 }
 
 // Writes the 32 counts of word X (bytes) and folds its solution count and max.
-__device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t planes[10], uint8_t *cost,
+template <int NPL>
+__device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t planes[NPL], uint8_t *cost,
                                           unsigned long long &nsol, uint32_t &mx) {
     const uint32_t valid = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
     uint32_t bytes[8];
     planes_to_bytes(planes, bytes);
     uint32_t any = 0;
+    uint32_t over = 0;
 #pragma unroll
-    for (int q = 0; q < 10; ++q) any |= planes[q];
+    for (int q = 0; q < NPL; ++q) {
+        any |= planes[q];
+        if (q >= 8) over |= planes[q];
+    }
     nsol += __popc(~any & valid);
-    const uint32_t over = (planes[8] | planes[9]) & valid;
+    over &= valid;
     uint32_t bm = 0;
     if (n >= 5) {
 #pragma unroll
@@ -166,7 +182,7 @@ __device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t plan
         for (uint32_t b = 0; b < 32; ++b)
             if ((over >> b) & 1u) {
                 uint32_t c = 0;
-                for (int q = 0; q < 10; ++q) c |= ((planes[q] >> b) & 1u) << q;
+                for (int q = 0; q < NPL; ++q) c |= ((planes[q] >> b) & 1u) << q;
                 bm = max(bm, c);
             }
     }
@@ -183,10 +199,11 @@ __device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t plan
 constexpr int SUB_WORDS = 2 * CT_THREADS;  // words per block step
 constexpr int SUB_BITS = 14;                // log2(32 SUB_WORDS): variables >= 14 are constant over a step
 
-// Keeps the clauses of srec[0, m) that can be violated somewhere in the words
-// [base, base + SUB_WORDS), reduced to variables 5..13, in alive[0, *count),
-// zero-padded to a multiple of 16.  Called by all threads of the block.
-__device__ __forceinline__ int filter_clauses(uint32_t base, int m, const uint4 *srec, uint4 *alive, int *count) {
+// Keeps the clauses of recs[0, m) (m <= CT_CHUNK; shared or global memory)
+// that can be violated somewhere in the words [base, base + SUB_WORDS),
+// reduced to variables 5..13, in alive[0, *count), zero-padded to a multiple
+// of 16.  Called by all threads of the block.
+__device__ __forceinline__ int filter_clauses(uint32_t base, int m, const uint4 *recs, uint4 *alive, int *count) {
     constexpr uint32_t MID = (1u << SUB_BITS) - 32u;  // variables 5..13
     const uint32_t xu = base << 5;                     // x bits >= 14 of the step (bits < 14 are zero)
     if (threadIdx.x == 0) *count = 0;
@@ -197,7 +214,7 @@ __device__ __forceinline__ int filter_clauses(uint32_t base, int m, const uint4 
         uint4 r = make_uint4(0, 0, 0, 0);
         bool keep = false;
         if (i < m) {
-            r = srec[i];
+            r = recs[i];
             const uint32_t umask = r.x & ~MID & ~31u;
             const uint32_t tu = (xu ^ r.y) & umask;
             const bool at = tu == umask, af = tu == 0u;  // uniform literals all true / all false
@@ -219,8 +236,11 @@ __device__ __forceinline__ int filter_clauses(uint32_t base, int m, const uint4 
 
 // One table: each block steps through SUB_WORDS consecutive words at a time;
 // thread t takes words base + t and base + CT_THREADS + t, so every clause
-// record loaded from shared memory serves 64 assignments.
-__device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *srec, uint4 *alive, int *acount,
+// record loaded from shared memory serves 64 assignments.  recs holds the m
+// records (shared memory when m <= CT_CHUNK, else global), taken CT_CHUNK at a
+// time.
+template <int NPL>
+__device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *recs, uint4 *alive, int *acount,
                                                 uint8_t *cost, unsigned long long *stats) {
     const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
     const uint64_t steps = (words + SUB_WORDS - 1) / SUB_WORDS;
@@ -228,15 +248,21 @@ __device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *srec,
     uint32_t mx = 0;
     for (uint64_t sb = blockIdx.x; sb < steps; sb += gridDim.x) {
         const uint32_t base = (uint32_t)(sb * SUB_WORDS);
-        const int c16 = filter_clauses(base, m, srec, alive, acount);
         const uint64_t X0 = base + threadIdx.x, X1 = X0 + CT_THREADS;
-        if (X0 < words) {
-            uint32_t p0[10], p1[10];
-            count_words2((uint32_t)X0, (uint32_t)(X1 < words ? X1 : X0), c16, alive, p0, p1);
-            emit_word(n, X0, p0, cost, nsol, mx);
-            if (X1 < words) emit_word(n, X1, p1, cost, nsol, mx);
+        WordCounter<NPL> c0, c1;
+        for (int k0 = 0; k0 < m || k0 == 0; k0 += CT_CHUNK) {
+            const int mc = m - k0 < CT_CHUNK ? m - k0 : CT_CHUNK;
+            const int c16 = filter_clauses(base, mc, recs + k0, alive, acount);
+            if (X0 < words) count_words2<NPL>((uint32_t)X0, (uint32_t)(X1 < words ? X1 : X0), c16, alive, c0, c1);
+            __syncthreads();  // the list is rebuilt for the next chunk or step
         }
-        __syncthreads();  // the list is rebuilt for the next step
+        if (X0 < words) {
+            uint32_t p0[NPL], p1[NPL];
+            c0.planes(p0);
+            c1.planes(p1);
+            emit_word<NPL>(n, X0, p0, cost, nsol, mx);
+            if (X1 < words) emit_word<NPL>(n, X1, p1, cost, nsol, mx);
+        }
     }
     // warp then block reduction, one atomic pair per block
 #pragma unroll
@@ -264,42 +290,49 @@ __device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *srec,
     }
 }
 
-constexpr int MAX_M16 = (QAOA_MAX_M + 15) / 16 * 16;
-
+// One table, m <= CT_PARAM_M, the records passed as kernel parameters and
+// copied to shared memory once.
 __global__ void __launch_bounds__(CT_THREADS) cost_table_kernel(const __grid_constant__ CostParams prm, uint8_t *cost,
                                                                 unsigned long long *stats) {
-    __shared__ uint4 srec[MAX_M16];
-    __shared__ uint4 alive[MAX_M16];
+    __shared__ uint4 srec[CT_CHUNK];
+    __shared__ uint4 alive[CT_CHUNK];
     __shared__ int acount;
     for (int i = threadIdx.x; i < prm.m; i += CT_THREADS) {
         const ClauseRec r = prm.rec[i];
         srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
     }
     __syncthreads();
-    cost_table_body(prm.n, prm.m, srec, alive, &acount, cost, stats);
+    cost_table_body<NPL_SMALL>(prm.n, prm.m, srec, alive, &acount, cost, stats);
 }
 
 // Batched tables.  With ns == nullptr every instance has n qubits and its table
 // at costs + inst 2^n; otherwise instance inst has ns[inst] qubits and its table
-// at costs + offs[inst].
+// at costs + offs[inst].  Records of up to CT_CHUNK clauses are copied to
+// shared memory once; longer lists are read from global memory chunk by chunk.
+template <int NPL>
 __global__ void __launch_bounds__(CT_THREADS) cost_table_batch_kernel(int n, const int *ns, const uint64_t *offs,
                                                                       const ClauseRec *recs, const int *ms,
                                                                       int m_stride, uint8_t *costs,
                                                                       unsigned long long *stats) {
-    __shared__ uint4 srec[MAX_M16];
-    __shared__ uint4 alive[MAX_M16];
+    static_assert(sizeof(ClauseRec) == sizeof(uint4), "a clause record is one 16-byte load");
+    __shared__ uint4 srec[CT_CHUNK];
+    __shared__ uint4 alive[CT_CHUNK];
     __shared__ int acount;
     const int inst = blockIdx.y;
     const int m = ms[inst];
     const ClauseRec *g = recs + (size_t)inst * m_stride;
-    for (int i = threadIdx.x; i < m; i += CT_THREADS) {
-        const ClauseRec r = g[i];
-        srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
+    const uint4 *src = reinterpret_cast<const uint4 *>(g);
+    if (m <= CT_CHUNK) {
+        for (int i = threadIdx.x; i < m; i += CT_THREADS) {
+            const ClauseRec r = g[i];
+            srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
+        }
+        __syncthreads();
+        src = srec;
     }
-    __syncthreads();
     const int ni = ns ? ns[inst] : n;
     uint8_t *dst = ns ? costs + offs[inst] : costs + ((size_t)inst << n);
-    cost_table_body(ni, m, srec, alive, &acount, dst, stats + 2 * inst);
+    cost_table_body<NPL>(ni, m, src, alive, &acount, dst, stats + 2 * inst);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,26 +359,21 @@ int validate_instance(const naesat_instance *inst) {
 }
 
 int encode_instance(const naesat_instance *inst, ClauseRec *out) {
+    // bit b of COL[v] = bit v of b: the value of variable v < 5 at x = b (mod 32)
+    static const uint32_t COL[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
     const int m = inst->m, k = inst->k;
     for (int i = 0; i < m; ++i) {
-        uint32_t mask = 0, negp = 0;
+        uint32_t mask = 0, negp = 0, at = 0xFFFFFFFFu, af = 0xFFFFFFFFu;
         for (int j = 0; j < k; ++j) {
             const int v = inst->var[(size_t)i * k + j];
+            const uint32_t s = inst->neg[(size_t)i * k + j];
             mask |= 1u << v;
-            negp |= (uint32_t)inst->neg[(size_t)i * k + j] << v;
-        }
-        uint32_t at = 0, af = 0;
-        for (uint32_t b = 0; b < 32; ++b) {
-            bool all_t = true, all_f = true;
-            for (int j = 0; j < k; ++j) {
-                const int v = inst->var[(size_t)i * k + j];
-                if (v >= 5) continue;
-                const uint32_t lit = ((b >> v) & 1u) ^ (uint32_t)inst->neg[(size_t)i * k + j];
-                all_t = all_t && lit == 1u;
-                all_f = all_f && lit == 0u;
+            negp |= s << v;
+            if (v < 5) {
+                const uint32_t lit = s ? ~COL[v] : COL[v];  // bit b: the literal is true at b
+                at &= lit;
+                af &= ~lit;
             }
-            at |= (uint32_t)all_t << b;
-            af |= (uint32_t)all_f << b;
         }
         out[i] = ClauseRec{mask & ~31u, negp & ~31u, at, af};
     }
@@ -368,18 +396,35 @@ int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d
     const int gx = grid_for(words, batch);
     if (gx < 0) return QAOA_ECUDA;
     profile_before(K_COST_TABLE, stream);
-    cost_table_batch_kernel<<<dim3(gx, batch), CT_THREADS, 0, stream>>>(n, d_ns, d_offs, d_recs, d_m, m_stride, d_costs,
-                                                                        d_stats);
+    if (m_stride <= CT_PARAM_M)
+        cost_table_batch_kernel<NPL_SMALL><<<dim3(gx, batch), CT_THREADS, 0, stream>>>(n, d_ns, d_offs, d_recs, d_m,
+                                                                                     m_stride, d_costs, d_stats);
+    else
+        cost_table_batch_kernel<NPL_LARGE><<<dim3(gx, batch), CT_THREADS, 0, stream>>>(n, d_ns, d_offs, d_recs, d_m,
+                                                                                     m_stride, d_costs, d_stats);
     return profile_after(K_COST_TABLE, stream);
 }
 
 int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned long long *d_stats,
-                          cudaStream_t stream, bool half) {
-    std::vector<char> buf(sizeof(CostParams));
-    CostParams *prm = reinterpret_cast<CostParams *>(buf.data());
+                          cudaStream_t stream, bool half, void *d_big) {
     // the kernel uses n only for the number of assignments: the half table is
     // the first 2^(n-1) of them (variable n - 1 is 0 there)
-    prm->n = half ? inst->n - 1 : inst->n;
+    const int n = half ? inst->n - 1 : inst->n;
+    if (inst->m > CT_PARAM_M) {
+        // records in global memory: d_big holds the m records then the count
+        if (!d_big) return set_error(QAOA_EINVAL, "m=%d needs device space for the clause records", inst->m);
+        std::vector<ClauseRec> rec((size_t)inst->m);
+        encode_instance(inst, rec.data());
+        ClauseRec *d_rec = reinterpret_cast<ClauseRec *>(d_big);
+        int *d_m = reinterpret_cast<int *>(d_rec + inst->m);
+        // pageable sources: the copies return once the data is staged
+        QAOA_CUDA_TRY(cudaMemcpyAsync(d_rec, rec.data(), rec.size() * sizeof(ClauseRec), cudaMemcpyHostToDevice, stream));
+        QAOA_CUDA_TRY(cudaMemcpyAsync(d_m, &inst->m, sizeof(int), cudaMemcpyHostToDevice, stream));
+        return launch_cost_table_batch(1, n, nullptr, nullptr, d_rec, d_m, inst->m, d_cost, d_stats, stream);
+    }
+    std::vector<char> buf(sizeof(CostParams));
+    CostParams *prm = reinterpret_cast<CostParams *>(buf.data());
+    prm->n = n;
     prm->m = inst->m;
     encode_instance(inst, prm->rec);
     const uint64_t words = prm->n >= 5 ? (1ull << (prm->n - 5)) : 1ull;
@@ -389,6 +434,8 @@ int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned
     cost_table_kernel<<<gx, CT_THREADS, 0, stream>>>(*prm, d_cost, d_stats);
     return profile_after(K_COST_TABLE, stream);
 }
+
+size_t cost_table_big_bytes(int m) { return m > CT_PARAM_M ? (size_t)m * sizeof(ClauseRec) + 16 : 0; }
 
 }  // namespace qaoa
 
@@ -402,11 +449,11 @@ static int cost_table_common(const naesat_instance *inst, uint8_t *d_cost, uint6
     if (half && inst->n < 6) return set_error(QAOA_ERANGE, "half table needs n >= 6 (n=%d)", inst->n);
     cudaStream_t stream = (cudaStream_t)stream_;
     Scratch *sc = nullptr;
-    rc = scratch_for(stream, 64, 64, &sc);
+    rc = scratch_for(stream, 256 + cost_table_big_bytes(inst->m), 64, &sc);
     if (rc) return rc;
     unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(sc->dev);
     QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 2 * sizeof(unsigned long long), stream));
-    rc = launch_cost_table_one(inst, d_cost, d_stats, stream, half);
+    rc = launch_cost_table_one(inst, d_cost, d_stats, stream, half, reinterpret_cast<char *>(sc->dev) + 256);
     if (rc) return rc;
     if (!n_sol && !max_cost && inst->m <= 255) return QAOA_OK;
     unsigned long long *h = reinterpret_cast<unsigned long long *>(sc->host);

@@ -622,7 +622,7 @@ struct PassKernels {
     HighSet<R, WROW, true> wide;
     HighSet<R, WROW, false> wide_part;
     cudaError_t init() {
-        const int big = (int)pass_smem<R>(true, QAOA_MAX_M);
+        const int big = (int)pass_smem<R>(true, MAX_TABLE - 1);
         std::vector<KPtr> ks;
         low.all(ks);
         low_z2.all(ks);
@@ -906,6 +906,7 @@ static int evolve_common(int batch, int n, const uint8_t *d_cost, int m, int p, 
     const double scale = z2 ? 2.0 : 1.0;  // each stored amplitude stands for x and not x
     cudaStream_t stream = (cudaStream_t)stream_;
     const bool want = p_succ || norm;
+    m = table_top(m);  // from here m bounds the phase tables only
     EvolveReq r{batch, n, m, p, dtype, flags, d_cost, d_state, adj, gamma, beta, nullptr};
     Scratch *sc = nullptr;
     if (n <= small_n_limit(dtype) && !adj) {

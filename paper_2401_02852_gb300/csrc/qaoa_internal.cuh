@@ -134,8 +134,11 @@ LayerCoef layer_coef(double beta, int sign);
 // the host; cast to the state's element type by the caller).
 void phase_table(double gamma, double scale, int m, double *re, double *im);
 
+// Largest cost a phase table indexes.  The cost table is uint8, so
+// C(x) <= 255 whatever m is: a table holds entries 0..table_top(m).
+inline int table_top(int m) { return m < 255 ? m : 255; }
 // Number of clause-count entries a phase table must hold.
-constexpr int MAX_TABLE = QAOA_MAX_M + 1;
+constexpr int MAX_TABLE = 256;
 
 // ---------------------------------------------------------------------------
 // Cost-table internals shared by the cost-table and serving code.
@@ -155,9 +158,12 @@ int validate_instance(const naesat_instance *inst);
 int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d_offs, const ClauseRec *d_recs,
                             const int *d_m, int m_stride, uint8_t *d_costs, unsigned long long *d_stats,
                             cudaStream_t stream);
-// One table with the clause records passed as kernel parameters (no staging).
+// One table.  Up to 1023 clauses the records go as kernel parameters (no
+// staging); a longer list is copied to d_big (device, cost_table_big_bytes(m)
+// bytes, 16-byte aligned) and counted chunk by chunk.
 int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned long long *d_stats,
-                          cudaStream_t stream, bool half = false);
+                          cudaStream_t stream, bool half, void *d_big);
+size_t cost_table_big_bytes(int m);
 
 // Multi-pass evolution of `batch` states (device side only, no host sync).
 // `tables` holds p layers x (m + 1) complex FP64 entries (interleaved).

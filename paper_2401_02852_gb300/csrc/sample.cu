@@ -9,10 +9,17 @@
 // differs from a sequential FP64 scan only through the summation order, i.e.
 // only for a u_j within rounding of a step of F.
 //
-//   1. block_sums_kernel: one FP64 sum per block of 2^SB amplitudes;
-//   2. block_prefix_kernel: inclusive prefix of the block sums, fixed order;
-//   3. draw_kernel: one warp per draw: binary search over the block prefix,
-//      then a warp-wide FP64 scan through the chosen block.
+// Two-level prefix.  An entry is 32 consecutive amplitudes, a group 256
+// entries (2^13 amplitudes).
+//   1. entry_scan_kernel: one CTA per group: each thread sums one entry in
+//      index order, then the CTA forms the inclusive prefix Q of its 256 entry
+//      sums (fixed order) and writes the group total;
+//   2. block_prefix_kernel: inclusive prefix P of the group totals, fixed order;
+//   3. draw_kernel: one warp per draw: 32-way searches over P and over the
+//      group's Q, then one FP64 warp scan over the chosen entry's 32
+//      amplitudes.
+// GB300's FP64 pipe is narrow, so a draw forms only those 32 probabilities;
+// the searches compare stored sums.
 // With QAOA_Z2_HALF the stored half holds the x with bit n-1 clear and
 // |psi(not x)| = |psi(x)| (Sec. 2.2's global flip): t = u 2 F_half picks the
 // stored x (t < F_half) or the complement of the x drawn at t - F_half.
@@ -25,9 +32,10 @@
 
 namespace qaoa {
 
-constexpr int SB = 13;           // log2 amplitudes per block
-constexpr int SUM_PT = 256;      // threads of the block-sum kernel
-constexpr int PREFIX_PT = 1024;  // threads of the prefix kernel
+constexpr int ENTRY_BITS = 5;    // log2 amplitudes per entry
+constexpr int GROUP_BITS = 8;    // log2 entries per group
+constexpr int GROUP = 1 << GROUP_BITS;
+constexpr int PREFIX_PT = 1024;  // threads of the group-prefix kernel
 constexpr int DRAW_WARPS = 8;    // draws per CTA of the draw kernel
 
 template <typename V>
@@ -36,102 +44,157 @@ __device__ __forceinline__ double prob(const V &z) {
     return re * re + im * im;
 }
 
-// sums[inst][b] = sum of |psi|^2 over block b (2^SB amplitudes, or the whole
-// stored state when it is smaller) of instance inst = blockIdx.y.
+// Entry and group counts of a stored state of 2^ns amplitudes.
+__host__ __device__ __forceinline__ uint64_t entry_count(int ns) {
+    return ns > ENTRY_BITS ? 1ull << (ns - ENTRY_BITS) : 1ull;
+}
+__host__ __device__ __forceinline__ uint64_t group_count(int ns) {
+    return (entry_count(ns) + GROUP - 1) >> GROUP_BITS;
+}
+
+// Group g = blockIdx.x of instance blockIdx.y: Q[e] = sum of the entry sums of
+// the group up to entry e (inclusive), G[g] = the group's total (= Q at its
+// last entry).  The running sums are serial within each warp's 32 entries and
+// offset by the serial sums of the earlier warps' totals, so Q is
+// nondecreasing and Q[e] > Q[e - 1] only where entry e has a nonzero sum.
 template <typename V>
-__global__ void __launch_bounds__(SUM_PT) block_sums_kernel(const V *states, int ns, uint64_t nb, double *sums) {
-    const uint64_t N = 1ull << ns;
-    const V *st = states + ((uint64_t)blockIdx.y << ns);
-    const uint64_t lo = (uint64_t)blockIdx.x << SB;
-    const uint64_t hi = lo + (1ull << SB) < N ? lo + (1ull << SB) : N;
+__global__ void __launch_bounds__(GROUP) entry_scan_kernel(const V *states, int ns, double *Q, double *G) {
+    __shared__ double run[GROUP];
+    __shared__ double off[GROUP / 32];
+    const uint64_t N = 1ull << ns, ne = entry_count(ns), ng = group_count(ns);
+    const uint64_t inst = blockIdx.y;
+    const V *st = states + (inst << ns);
+    const uint64_t e = ((uint64_t)blockIdx.x << GROUP_BITS) + threadIdx.x;
     double s = 0.0;
-    for (uint64_t x = lo + threadIdx.x; x < hi; x += SUM_PT) s += prob(st[x]);
-    double v[1] = {s};
-    block_sum<1, SUM_PT>(v);
-    if (threadIdx.x == 0) sums[(uint64_t)blockIdx.y * nb + blockIdx.x] = v[0];
+    if (e < ne) {
+        const uint64_t x0 = e << ENTRY_BITS, x1 = x0 + 32 < N ? x0 + 32 : N;
+        for (uint64_t x = x0; x < x1; ++x) s += prob(st[x]);
+    }
+    run[threadIdx.x] = s;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {  // serial running sums of this warp's entries
+        double r = 0.0;
+        for (int i = 0; i < 32; ++i) {
+            r += run[32 * w + i];
+            run[32 * w + i] = r;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // warp totals -> offsets, in order
+        double r = 0.0;
+        for (int i = 0; i < GROUP / 32; ++i) {
+            off[i] = r;
+            r = r + run[32 * i + 31];
+        }
+    }
+    __syncthreads();
+    const double q = off[w] + run[threadIdx.x];
+    if (e < ne) Q[inst * ne + e] = q;
+    const uint64_t left = ne - ((uint64_t)blockIdx.x << GROUP_BITS);  // entries of this group
+    if ((uint64_t)threadIdx.x == (left < (uint64_t)GROUP ? left : (uint64_t)GROUP) - 1) G[inst * ng + blockIdx.x] = q;
 }
 
 // In place, per instance (one CTA each): sums[b] <- sums[0] + ... + sums[b].
-// Each thread adds a contiguous chunk in order, thread 0 turns the chunk
-// totals into offsets in order, then each thread writes its running sums.
+// Each thread forms serial running sums over a contiguous chunk, thread 0
+// turns the chunk totals into offsets in order, then each thread adds its
+// offset; the last value of a chunk equals the next chunk's offset, so the
+// result is nondecreasing and rises only where a sum is nonzero.
 __global__ void __launch_bounds__(PREFIX_PT) block_prefix_kernel(double *sums, uint64_t nb) {
     __shared__ double chunk[PREFIX_PT];
     double *s = sums + (uint64_t)blockIdx.x * nb;
     const uint64_t per = (nb + PREFIX_PT - 1) / PREFIX_PT;
     const uint64_t lo = threadIdx.x * per < nb ? threadIdx.x * per : nb;
     const uint64_t hi = lo + per < nb ? lo + per : nb;
-    double c = 0.0;
-    for (uint64_t i = lo; i < hi; ++i) c += s[i];
-    chunk[threadIdx.x] = c;
+    double r = 0.0;
+    for (uint64_t i = lo; i < hi; ++i) {
+        r += s[i];
+        s[i] = r;
+    }
+    chunk[threadIdx.x] = r;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double run = 0.0;
+        double acc = 0.0;
         for (int t = 0; t < PREFIX_PT; ++t) {
             const double v = chunk[t];
-            chunk[t] = run;
-            run += v;
+            chunk[t] = acc;
+            acc = acc + v;
         }
     }
     __syncthreads();
-    double run = chunk[threadIdx.x];
-    for (uint64_t i = lo; i < hi; ++i) {
-        run += s[i];
-        s[i] = run;
+    const double o = chunk[threadIdx.x];
+    for (uint64_t i = lo; i < hi; ++i) s[i] = o + s[i];
+}
+
+// Smallest i in [0, len) with A[i] > key (A nondecreasing, A[len - 1] > key),
+// or with A[i] >= A[len - 1] when `edge`; a 32-way search by the whole warp.
+__device__ __forceinline__ uint64_t warp_search(const double *A, uint64_t len, double key, bool edge) {
+    const int lane = threadIdx.x & 31;
+    if (edge) key = A[len - 1];
+    uint64_t lo = 0, hi = len;  // the answer is in [lo, hi)
+    while (hi - lo > 1) {
+        const uint64_t stride = (hi - lo + 31) / 32;
+        uint64_t i = lo + (uint64_t)(lane + 1) * stride - 1;
+        if (i > hi - 1) i = hi - 1;
+        const double v = A[i];
+        const unsigned ok = __ballot_sync(0xFFFFFFFFu, edge ? v >= key : v > key);
+        const uint64_t f = (uint64_t)(__ffs(ok) - 1);  // A[hi - 1] qualifies, so ok != 0
+        const uint64_t nlo = lo + f * stride;
+        hi = nlo + stride < hi ? nlo + stride : hi;
+        lo = nlo;
     }
+    return lo;
 }
 
 // One warp per draw j of instance blockIdx.y: x_j = min { x : F(x) > t } with
-// t = u_j F_total; an x of probability zero never wins.  When no x qualifies
-// (t at F_total by rounding, or inside a block past its rounded sum) the last
-// x of nonzero probability of the block is taken.
+// t = u_j F_total; an x of probability zero never wins.  When rounding leaves
+// no x qualifying at some level (t at F_total, or the remainder at a group's or
+// an entry's rounded total) the last x of nonzero probability under the
+// chosen group and entry is taken.
 template <typename V>
-__global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, int ns, int z2, const double *prefix,
-                                                                 uint64_t nb, int k, const double *u, uint64_t *xs) {
+__global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, int ns, int z2, const double *Q,
+                                                                 const double *P, int k, const double *u,
+                                                                 uint64_t *xs) {
     const int lane = threadIdx.x & 31;
     const uint64_t j = (uint64_t)blockIdx.x * DRAW_WARPS + (threadIdx.x >> 5);
     if (j >= (uint64_t)k) return;  // whole warps leave together
     const uint64_t inst = blockIdx.y;
-    const uint64_t N = 1ull << ns;
+    const uint64_t N = 1ull << ns, ne = entry_count(ns), ng = group_count(ns);
     const V *st = states + (inst << ns);
-    const double *P = prefix + inst * nb;
-    const double total = P[nb - 1];
+    const double *Pi = P + inst * ng;
+    const double total = Pi[ng - 1];
     double t = u[inst * (uint64_t)k + j] * (z2 ? 2.0 * total : total);
     bool flip = false;
-    if (z2 && t >= total) {
+    if (z2 && total > 0.0 && t >= total) {
         flip = true;
         t -= total;
     }
-    // smallest block b with P[b] > t; when rounding left t at F_total, the
-    // block holding the last x of nonzero probability (smallest P[b] >= total)
-    const bool edge = !(t < total);
-    uint64_t lo = 0, hi = nb - 1;
-    while (lo < hi) {
-        const uint64_t mid = lo + (hi - lo) / 2;
-        if (edge ? P[mid] >= total : P[mid] > t)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    double rest = edge ? HUGE_VAL : t - (lo > 0 ? P[lo - 1] : 0.0);
-    const uint64_t x0 = lo << SB, x1 = x0 + (1ull << SB) < N ? x0 + (1ull << SB) : N;
-    uint64_t found = ~0ull, last_nz = x0;
-    for (uint64_t c = x0; c < x1 && found == ~0ull; c += 32) {
-        const uint64_t x = c + lane;
-        const double w = x < x1 ? prob(st[x]) : 0.0;
-        double incl = w;
+    // group
+    bool edge = !(t < total);
+    const uint64_t g = warp_search(Pi, ng, t, edge);
+    double rest = t - (g > 0 ? Pi[g - 1] : 0.0);
+    // entry within the group
+    const uint64_t e0 = g << GROUP_BITS;
+    const uint64_t glen = ne - e0 < (uint64_t)GROUP ? ne - e0 : (uint64_t)GROUP;
+    const double *Qg = Q + inst * ne + e0;
+    edge = edge || !(rest < Qg[glen - 1]);
+    const uint64_t e = warp_search(Qg, glen, rest, edge);
+    rest -= e > 0 ? Qg[e - 1] : 0.0;
+    // amplitude within the entry
+    const uint64_t x = ((e0 + e) << ENTRY_BITS) + (uint64_t)lane;
+    const double w = x < N ? prob(st[x]) : 0.0;
+    double incl = w;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const unsigned hit = __ballot_sync(0xFFFFFFFFu, w > 0.0 && incl > rest);
-        const unsigned nz = __ballot_sync(0xFFFFFFFFu, w > 0.0);
-        if (hit) found = c + (uint64_t)(__ffs(hit) - 1);
-        if (nz) last_nz = c + (uint64_t)(31 - __clz(nz));
-        rest -= __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
     }
-    if (found == ~0ull) found = last_nz;
+    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && w > 0.0 && incl > rest);
+    const unsigned nz = __ballot_sync(0xFFFFFFFFu, w > 0.0);
+    // the chosen entry has a nonzero sum (nz != 0) unless the state's norm is 0
+    const int pick = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);
     if (lane == 0) {
+        const uint64_t found = ((e0 + e) << ENTRY_BITS) + (uint64_t)pick;
         const uint64_t full = (1ull << (ns + (z2 ? 1 : 0))) - 1ull;
         xs[inst * (uint64_t)k + j] = flip ? (~found & full) : found;
     }
@@ -163,30 +226,31 @@ static int sample_impl(int batch, int n, const uint8_t *d_costs, const void *d_s
     if (running_time && !d_costs) return set_error(QAOA_EINVAL, "running time needs the cost table");
     if (!running_time && !d_x) return set_error(QAOA_EINVAL, "nowhere to put the draws");
     const int ns = z2 ? n - 1 : n;  // index bits of the stored state and of its table
-    const uint64_t nb = ((1ull << ns) + (1ull << SB) - 1) >> SB;
-    const size_t pre = sizeof(double) * nb * (size_t)batch;
+    const uint64_t ne = entry_count(ns), ng = group_count(ns);
+    const size_t qb = sizeof(double) * ne * (size_t)batch;
+    const size_t pre = qb + ((sizeof(double) * ng * (size_t)batch + 255) & ~(size_t)255);
     const size_t xb = d_x ? 0 : sizeof(uint64_t) * (size_t)k * batch;
     const size_t fb = sizeof(int) * (size_t)batch;
     Scratch *sc = nullptr;
     int rc = scratch_for(stream, pre + xb + fb + 64, fb + 64, &sc);
     if (rc) return rc;
     char *dev = reinterpret_cast<char *>(sc->dev);
-    double *d_pre = reinterpret_cast<double *>(dev);
+    double *d_q = reinterpret_cast<double *>(dev);
+    double *d_pre = reinterpret_cast<double *>(dev + qb);
     uint64_t *xs = d_x ? d_x : reinterpret_cast<uint64_t *>(dev + pre);
     int *d_first = reinterpret_cast<int *>(dev + pre + xb);
+    const dim3 draw_grid((unsigned)((k + DRAW_WARPS - 1) / DRAW_WARPS), batch);
     profile_before(K_SAMPLE, stream);
     if (dtype == QAOA_C64) {
         const float2 *st = reinterpret_cast<const float2 *>(d_states);
-        block_sums_kernel<float2><<<dim3((unsigned)nb, batch), SUM_PT, 0, stream>>>(st, ns, nb, d_pre);
-        block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, nb);
-        draw_kernel<float2><<<dim3((unsigned)((k + DRAW_WARPS - 1) / DRAW_WARPS), batch), DRAW_WARPS * 32, 0, stream>>>(
-            st, ns, z2 ? 1 : 0, d_pre, nb, k, d_u, xs);
+        entry_scan_kernel<float2><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+        block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, ng);
+        draw_kernel<float2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_pre, k, d_u, xs);
     } else {
         const double2 *st = reinterpret_cast<const double2 *>(d_states);
-        block_sums_kernel<double2><<<dim3((unsigned)nb, batch), SUM_PT, 0, stream>>>(st, ns, nb, d_pre);
-        block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, nb);
-        draw_kernel<double2><<<dim3((unsigned)((k + DRAW_WARPS - 1) / DRAW_WARPS), batch), DRAW_WARPS * 32, 0, stream>>>(
-            st, ns, z2 ? 1 : 0, d_pre, nb, k, d_u, xs);
+        entry_scan_kernel<double2><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+        block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, ng);
+        draw_kernel<double2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_pre, k, d_u, xs);
     }
     rc = profile_after(K_SAMPLE, stream);
     if (rc || !running_time) return rc;

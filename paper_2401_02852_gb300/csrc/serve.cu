@@ -111,14 +111,15 @@ static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
     const size_t N = (size_t)1 << (z2 ? q.n - 1 : q.n);
     int rc;
     naesat_instance inst{q.n, q.m, q.k, q.var.data(), q.neg.data()};
-    // results layout in staging: [0..2) stats (u64), [2..4) p_succ, norm
-    if ((rc = ensure_stage(s, 64))) return rc;
+    // staging: [0..2) stats (u64), [2..4) p_succ, norm; from byte 256 the
+    // clause records of a list too long for kernel parameters
+    if ((rc = ensure_stage(s, 256 + cost_table_big_bytes(q.m)))) return rc;
     QAOA_CUDA_TRY(cudaMallocAsync(&s.d_cost, N, s.stream));
     QAOA_CUDA_TRY(cudaMallocAsync(&s.d_state, N * es_of(dtype), s.stream));
     unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(s.d_stage);
     double *d_res = reinterpret_cast<double *>(s.d_stage + 16);
     QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 16, s.stream));
-    if ((rc = launch_cost_table_one(&inst, (uint8_t *)s.d_cost, d_stats, s.stream, z2))) return rc;
+    if ((rc = launch_cost_table_one(&inst, (uint8_t *)s.d_cost, d_stats, s.stream, z2, s.d_stage + 256))) return rc;
     const int gx = pass_grid_x(dtype, z2 ? q.n - 1 : q.n, 1);
     if (gx < 0) return QAOA_ECUDA;
     if (s.part_cap < (size_t)gx * 2) {
@@ -126,7 +127,7 @@ static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
         QAOA_CUDA_TRY(cudaMalloc((void **)&s.d_part, (size_t)gx * 2 * sizeof(double)));
         s.part_cap = (size_t)gx * 2;
     }
-    EvolveReq r{1, q.n, q.m, q.p, dtype, sv->o.flags, (const uint8_t *)s.d_cost, s.d_state, nullptr,
+    EvolveReq r{1, q.n, table_top(q.m), q.p, dtype, sv->o.flags, (const uint8_t *)s.d_cost, s.d_state, nullptr,
                 q.gamma.data(), q.beta.data(), d_res};
     if ((rc = evolve_device_impl(r, s.stream, s.d_part, gx))) return rc;
     QAOA_CUDA_TRY(cudaMemcpyAsync(s.h_stage, s.d_stage, 32, cudaMemcpyDeviceToHost, s.stream));
@@ -146,7 +147,7 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
     for (auto &q : batch) {
         m_stride = std::max(m_stride, q->m);
         max_n = std::max(max_n, q->n);
-        tab_n += (size_t)std::max(q->p, 1) * (q->m + 1);
+        tab_n += (size_t)std::max(q->p, 1) * (table_top(q->m) + 1);
         coef_n += (size_t)std::max(q->p, 1);
         cost_bytes += ((size_t)1 << q->n);
     }
@@ -183,16 +184,17 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
         h_n[b] = q.n;
         h_off[b] = boff;
         const int pl = std::max(q.p, 1);
-        re.resize(q.m + 1);
-        im.resize(q.m + 1);
+        const int mt = table_top(q.m);
+        re.resize(mt + 1);
+        im.resize(mt + 1);
         for (int l = 0; l < pl; ++l) {
             LayerCoef k = q.p > 0 ? layer_coef(q.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
             double scale = std::pow(k.sigma, q.n);
             if (l == 0) scale *= std::pow(2.0, -0.5 * q.n);
-            phase_table(q.p > 0 ? q.gamma[l] : 0.0, scale, q.m, re.data(), im.data());
-            for (int c = 0; c <= q.m; ++c) {
-                h_tab[2 * (toff + (size_t)l * (q.m + 1) + c)] = re[c];
-                h_tab[2 * (toff + (size_t)l * (q.m + 1) + c) + 1] = im[c];
+            phase_table(q.p > 0 ? q.gamma[l] : 0.0, scale, mt, re.data(), im.data());
+            for (int c = 0; c <= mt; ++c) {
+                h_tab[2 * (toff + (size_t)l * (mt + 1) + c)] = re[c];
+                h_tab[2 * (toff + (size_t)l * (mt + 1) + c) + 1] = im[c];
             }
             h_coef[4 * (coff + l)] = k.A;
             h_coef[4 * (coff + l) + 1] = k.B;
@@ -204,12 +206,12 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
         j.state = nullptr;
         j.result = reinterpret_cast<double *>(d + o_res) + 2 * b;
         j.n = q.n;
-        j.m = q.m;
+        j.m = mt;
         j.p = q.p;
         j.table_off = (int)toff;
         j.coef_off = (int)coff;
         h_jobs[b] = j;
-        toff += (size_t)pl * (q.m + 1);
+        toff += (size_t)pl * (mt + 1);
         coff += pl;
         boff += (size_t)1 << q.n;
     }

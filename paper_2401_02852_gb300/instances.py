@@ -15,12 +15,18 @@ Phase Transitions" for F_k(n, m)):
   across clauses allowed: "with replacement");
 * each literal is negated independently with probability 1/2.
 
+The paper's own evaluation draws CNF(n, k, r_hat_k) with m ~ Poisson(r_hat_k n)
+at the threshold estimate r_hat_k (``threshold_density``, ``protocol_instance``);
+its clauses come from ``draw_clauses_keys``, the same distribution drawn with
+whole-array operations.
+
 Literal j of clause i is the variable ``var[i, j]`` (0-based; variable v is
 bit v of the assignment index x) negated when ``neg[i, j] == 1``.
 """
 from __future__ import annotations
 
 import hashlib
+import math
 from dataclasses import dataclass
 from typing import Callable, Optional
 
@@ -66,6 +72,36 @@ def draw_clauses(n: int, k: int, m: int, rng: np.random.Generator):
         var[i] = rng.choice(n, size=k, replace=False)
         neg[i] = rng.integers(0, 2, size=k)
     return var, neg
+
+
+def draw_clauses_keys(n: int, k: int, m: int, rng: np.random.Generator):
+    """m clauses as in ``draw_clauses``, drawn as arrays: the k smallest of n
+    iid uniform keys per clause (a uniformly random permutation's first k
+    entries: a uniform k-subset in a uniformly random order), then k fair
+    negations per clause."""
+    if not (1 <= k <= n):
+        raise ValueError(f"need 1 <= k <= n, got k={k}, n={n}")
+    keys = rng.random((m, n))
+    var = np.argsort(keys, axis=1)[:, :k].astype(np.int32)
+    neg = rng.integers(0, 2, size=(m, k), dtype=np.uint8)
+    return np.ascontiguousarray(var), neg
+
+
+def threshold_density(k: int) -> float:
+    """r_hat_k = (2^(k-1) - 1/2 - 1/(4 ln 2)) ln 2: the asymptotic NAE-k-SAT
+    satisfiability threshold without its o_k(1) term (Sec. "QAOA Procedure",
+    Eq. for r_hat^NAE_k)."""
+    ln2 = math.log(2.0)
+    return (2.0 ** (k - 1) - 0.5 - 1.0 / (4.0 * ln2)) * ln2
+
+
+def protocol_instance(tag: str, n: int, k: int, index: int, attempt: int = 0) -> Instance:
+    """Attempt ``attempt`` of instance ``index`` of CNF(n, k, r_hat_k): m ~
+    Poisson(r_hat_k n) (Def. of CNF(n, k, r)), clauses from ``draw_clauses_keys``."""
+    rng = rng_for(tag, n, k, index, attempt)
+    m = int(rng.poisson(threshold_density(k) * n))
+    var, neg = draw_clauses_keys(n, k, m, rng)
+    return Instance(n=n, k=k, var=var, neg=neg, seed_key=(tag, n, k, index, attempt))
 
 
 def raw_instance(tag: str, n: int, k: int, r: float, index: int, attempt: int = 0,

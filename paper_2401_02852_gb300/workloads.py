@@ -7,7 +7,10 @@
   against central differences, then Adam on the shared angles;
 * ``sweep``:  median 1/p_succ versus n and its fitted exponent, and the median
   running time (bitstrings sampled until one satisfies) beside 1/E[p_succ];
-* ``batch``:  100 small instances (n = 12, p = 5, complex128) in one launch.
+* ``batch``:  100 small instances (n = 12, p = 5, complex128) in one launch;
+* ``protocol``: the paper's own evaluation (``protocol``): angles trained at
+  n = 12 per (k, p), then p_hat and median running times over satisfiable
+  CNF(n, k, r_hat_k) instances at n = 12..19, and the fitted exponents.
 
 Every function returns a JSON-serialisable dict.  All device work goes through
 the library's C ABI.
@@ -19,7 +22,7 @@ import time
 import numpy as np
 import torch
 
-from . import api, serve, sweep, train
+from . import api, protocol, serve, sweep, train
 from . import instances as gen
 
 
@@ -189,3 +192,14 @@ def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p:
                          "frac": flops / dt / fp64_nominal, "peak_source": "nominal"},
             "mean_psucc": float(np.mean(ps)),
             "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols))}
+
+
+def protocol_workload(ks=(9,), ps=(1, 2, 4, 8, 16, 32), count: int = 2500, lr: float = 1e-3) -> dict:
+    res = protocol.run_protocol(ks=ks, ps=ps, count=count, lr=lr)
+    evolve_s = sum(v["stats"]["evolve_s"] for v in res["by_k"].values())
+    amp_layers = sum(v["stats"]["amp_layers"] for v in res["by_k"].values())
+    draws = sum(v["stats"]["draws"] for v in res["by_k"].values())
+    sample_s = sum(v["stats"]["sample_s"] for v in res["by_k"].values())
+    res["evolve_amp_layer_per_s"] = amp_layers / evolve_s if evolve_s else None
+    res["draws_per_s"] = draws / sample_s if sample_s else None
+    return res

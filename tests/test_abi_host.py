@@ -96,6 +96,10 @@ def test_argument_validation_precedes_device_work(lib):
     assert b"repeated" in lib.qaoa_last_error()
     inst = _lib.NaesatInstance(40, 1, 3, var.ctypes.data, neg.ctypes.data)
     assert lib.naesat_cost_table(ctypes.byref(inst), ctypes.c_void_p(1), None, None, None) == _lib_code("ERANGE")
+    inst = _lib.NaesatInstance(20, 8192, 3, var.ctypes.data, neg.ctypes.data)  # one past the clause limit
+    assert lib.naesat_cost_table(ctypes.byref(inst), ctypes.c_void_p(1), None, None, None) == _lib_code("ERANGE")
+    assert lib.qaoa_evolve(20, ctypes.c_void_p(1), 8192, 0, None, None, 0, 0, ctypes.c_void_p(1),
+                           None, None, None) == _lib_code("ERANGE")
     g = np.array([0.1, float("nan")])
     assert lib.qaoa_evolve(20, ctypes.c_void_p(1), 10, 2, g.ctypes.data, g.ctypes.data, 0, 0, ctypes.c_void_p(1),
                            None, None, None) == _lib_code("EINVAL")
