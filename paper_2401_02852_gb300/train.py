@@ -71,9 +71,9 @@ def train_angles(costs: torch.Tensor, n: int, m: int, gamma0, beta0, steps: int 
         obj = torch.log(p).mean() if objective == "mean_log" else p.mean()
         (-obj).backward()
         opt.step()
-        trace.append((step, float(obj)))
+        trace.append((step, float(obj.detach())))
         if log:
-            log(step, float(obj))
+            log(step, float(obj.detach()))
         if checkpoint and ((step + 1) % checkpoint_every == 0 or step + 1 == steps):
             _save(checkpoint, gamma, beta, opt, step + 1, trace)
     return gamma.detach().numpy().copy(), beta.detach().numpy().copy(), trace
