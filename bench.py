@@ -415,6 +415,8 @@ def run_workload(args):
     elif args.workload == "sweep":
         res = workloads.sweep_workload(ns=range(args.sweep_n0, args.sweep_n1 + 1, 2), seeds=args.seeds,
                                        out_dir=args.out_dir)
+    elif args.workload == "sample":
+        res = workloads.sample_workload(n=args.n)
     elif args.workload == "protocol":
         res = workloads.protocol_workload(ks=tuple(int(k) for k in args.ks.split(",")),
                                           ps=tuple(int(p) for p in args.ps.split(",")),
@@ -442,7 +444,7 @@ def main():
     ap.add_argument("--no-z2", dest="z2", action="store_false", help="skip the halved-state measurement")
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="short serving run (Poisson 200/s) reported beside the headline; 0 skips it")
-    ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch", "protocol"], default="evolve")
+    ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch", "sample", "protocol"], default="evolve")
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--batch", type=int, default=256)

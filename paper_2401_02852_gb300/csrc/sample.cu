@@ -5,21 +5,24 @@
 //
 // Inverse-CDF sampling with caller-supplied uniforms u_j in [0, 1): draw j is
 // the smallest x with F(x) > u_j F_total, F(x) = sum_{y <= x} |psi(y)|^2.  The
-// probabilities are formed in FP64 from the stored amplitudes, so the result
-// differs from a sequential FP64 scan only through the summation order, i.e.
-// only for a u_j within rounding of a step of F.
+// sums are formed in FP64 (complex64 entry sums in double-float arithmetic
+// with exact squares, about 2^-44 relative), so the result differs from a
+// sequential FP64 scan only through rounding, i.e. only for a u_j within
+// rounding of a step of F.
 //
 // Two-level prefix.  An entry is 32 consecutive amplitudes, a group 256
 // entries (2^13 amplitudes).
 //   1. entry_scan_kernel: one CTA per group: each thread sums one entry in
-//      index order, then the CTA forms the inclusive prefix Q of its 256 entry
-//      sums (fixed order) and writes the group total;
+//      index order (complex64: on the FP32 pipes, see entry_sum), then the CTA
+//      forms the inclusive prefix Q of its 256 entry sums (fixed order) and
+//      writes the group total;
 //   2. block_prefix_kernel: inclusive prefix P of the group totals, fixed order;
 //   3. draw_kernel: one warp per draw: 32-way searches over P and over the
 //      group's Q, then one FP64 warp scan over the chosen entry's 32
 //      amplitudes.
-// GB300's FP64 pipe is narrow, so a draw forms only those 32 probabilities;
-// the searches compare stored sums.
+// GB300's FP64 pipe is narrow, so a draw forms only those 32 probabilities in
+// FP64; the searches compare the stored nonnegative sums as integers (the bit
+// patterns of doubles >= +0 order as the values do).
 // With QAOA_Z2_HALF the stored half holds the x with bit n-1 clear and
 // |psi(not x)| = |psi(x)| (Sec. 2.2's global flip): t = u 2 F_half picks the
 // stored x (t < F_half) or the complement of the x drawn at t - F_half.
@@ -42,6 +45,30 @@ template <typename V>
 __device__ __forceinline__ double prob(const V &z) {
     const double re = (double)z.x, im = (double)z.y;
     return re * re + im * im;
+}
+
+// Sum of |psi(x)|^2 over x in [x0, x1), in index order.  complex64: the
+// squares are exact as p + e (FMA form of Dekker's TwoProduct), each p is
+// added to a double-float accumulator with Knuth's TwoSum and the rounding
+// errors collect in its low word, all on the FP32 pipes; complex128: FP64.
+__device__ __forceinline__ double entry_sum(const float2 *st, uint64_t x0, uint64_t x1) {
+    float hi = 0.f, lo = 0.f;
+    for (uint64_t x = x0; x < x1; ++x) {
+        const float2 z = st[x];
+        const float pr = __fmul_rn(z.x, z.x), er = __fmaf_rn(z.x, z.x, -pr);
+        const float pi = __fmul_rn(z.y, z.y), ei = __fmaf_rn(z.y, z.y, -pi);
+        float s, e;
+        df_two_sum(hi, pr, s, e);
+        lo = __fadd_rn(lo, __fadd_rn(e, er));
+        df_two_sum(s, pi, hi, e);
+        lo = __fadd_rn(lo, __fadd_rn(e, ei));
+    }
+    return (double)hi + (double)lo;  // exact: hi + lo fits a double
+}
+__device__ __forceinline__ double entry_sum(const double2 *st, uint64_t x0, uint64_t x1) {
+    double s = 0.0;
+    for (uint64_t x = x0; x < x1; ++x) s += prob(st[x]);
+    return s;
 }
 
 // Entry and group counts of a stored state of 2^ns amplitudes.
@@ -68,7 +95,7 @@ __global__ void __launch_bounds__(GROUP) entry_scan_kernel(const V *states, int 
     double s = 0.0;
     if (e < ne) {
         const uint64_t x0 = e << ENTRY_BITS, x1 = x0 + 32 < N ? x0 + 32 : N;
-        for (uint64_t x = x0; x < x1; ++x) s += prob(st[x]);
+        s = entry_sum(st, x0, x1);
     }
     run[threadIdx.x] = s;
     __syncthreads();
@@ -126,18 +153,23 @@ __global__ void __launch_bounds__(PREFIX_PT) block_prefix_kernel(double *sums, u
     for (uint64_t i = lo; i < hi; ++i) s[i] = o + s[i];
 }
 
+// Doubles >= +0 compare as their bit patterns do (as signed 64-bit integers),
+// which keeps the searches off the FP64 pipe.
+__device__ __forceinline__ long long ord(double v) { return __double_as_longlong(v); }
+
 // Smallest i in [0, len) with A[i] > key (A nondecreasing, A[len - 1] > key),
 // or with A[i] >= A[len - 1] when `edge`; a 32-way search by the whole warp.
+// Every A[i] and key are >= +0.
 __device__ __forceinline__ uint64_t warp_search(const double *A, uint64_t len, double key, bool edge) {
     const int lane = threadIdx.x & 31;
-    if (edge) key = A[len - 1];
+    const long long kb = ord(edge ? A[len - 1] : key);
     uint64_t lo = 0, hi = len;  // the answer is in [lo, hi)
     while (hi - lo > 1) {
         const uint64_t stride = (hi - lo + 31) / 32;
         uint64_t i = lo + (uint64_t)(lane + 1) * stride - 1;
         if (i > hi - 1) i = hi - 1;
-        const double v = A[i];
-        const unsigned ok = __ballot_sync(0xFFFFFFFFu, edge ? v >= key : v > key);
+        const long long v = ord(A[i]);
+        const unsigned ok = __ballot_sync(0xFFFFFFFFu, edge ? v >= kb : v > kb);
         const uint64_t f = (uint64_t)(__ffs(ok) - 1);  // A[hi - 1] qualifies, so ok != 0
         const uint64_t nlo = lo + f * stride;
         hi = nlo + stride < hi ? nlo + stride : hi;
@@ -163,21 +195,23 @@ __global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, 
     const V *st = states + (inst << ns);
     const double *Pi = P + inst * ng;
     const double total = Pi[ng - 1];
-    double t = u[inst * (uint64_t)k + j] * (z2 ? 2.0 * total : total);
+    double uj = u[inst * (uint64_t)k + j];
+    uj = uj > 0.0 ? uj : 0.0;  // u <= 0 (or NaN) draws the first x of nonzero probability
+    double t = uj * (z2 ? 2.0 * total : total);
     bool flip = false;
-    if (z2 && total > 0.0 && t >= total) {
+    if (z2 && total > 0.0 && ord(t) >= ord(total)) {
         flip = true;
         t -= total;
     }
-    // group
-    bool edge = !(t < total);
+    // group (t, the sums and every remainder below are >= +0)
+    bool edge = ord(t) >= ord(total);
     const uint64_t g = warp_search(Pi, ng, t, edge);
     double rest = t - (g > 0 ? Pi[g - 1] : 0.0);
     // entry within the group
     const uint64_t e0 = g << GROUP_BITS;
     const uint64_t glen = ne - e0 < (uint64_t)GROUP ? ne - e0 : (uint64_t)GROUP;
     const double *Qg = Q + inst * ne + e0;
-    edge = edge || !(rest < Qg[glen - 1]);
+    edge = edge || ord(rest) >= ord(Qg[glen - 1]);
     const uint64_t e = warp_search(Qg, glen, rest, edge);
     rest -= e > 0 ? Qg[e - 1] : 0.0;
     // amplitude within the entry

@@ -8,6 +8,8 @@
 * ``sweep``:  median 1/p_succ versus n and its fitted exponent, and the median
   running time (bitstrings sampled until one satisfies) beside 1/E[p_succ];
 * ``batch``:  100 small instances (n = 12, p = 5, complex128) in one launch;
+* ``sample``: bitstring draws from the n = 30, p = 10 output state, and
+  running times of a batch of protocol-sized states (n = 19);
 * ``protocol``: the paper's own evaluation (``protocol``): angles trained at
   n = 12 per (k, p), then p_hat and median running times over satisfiable
   CNF(n, k, r_hat_k) instances at n = 12..19, and the fitted exponents.
@@ -202,4 +204,56 @@ def protocol_workload(ks=(9,), ps=(1, 2, 4, 8, 16, 32), count: int = 2500, lr: f
     sample_s = sum(v["stats"]["sample_s"] for v in res["by_k"].values())
     res["evolve_amp_layer_per_s"] = amp_layers / evolve_s if evolve_s else None
     res["draws_per_s"] = draws / sample_s if sample_s else None
+    return res
+
+
+def _event_ms(fn, reps: int) -> float:
+    """Mean device time of `fn` over `reps` calls on the current stream (CUDA events)."""
+    fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def sample_workload(n: int = 30, p: int = 10, draws: int = 1 << 24, batch: int = 2500, batch_n: int = 19,
+                    batch_k: int = 9, batch_p: int = 8, batch_draws: int = 4096, reps: int = 5) -> dict:
+    """Draw throughput of the sampler.  (a) One n = 30 state (the headline
+    evolution): the two-level prefix alone (one draw) and with `draws` draws.
+    (b) Running times of `batch` evolved CNF(batch_n, batch_k, r_hat) states,
+    `batch_draws` uniforms each, as the protocol's first sampling round."""
+    inst, _ = gen.satisfiable_instance("bench-n30", n, 5, 8.0, 0, lambda x: api.cost_table(x)[1])
+    cost = api.cost_table(inst)[0]
+    g, b = gen.linear_ramp(p)
+    state, _, _ = api.evolve(n, cost, inst.m, g, b, "c64")
+    u1 = gen.device_uniforms("sample-bench", (1,))
+    u = gen.device_uniforms("sample-bench", (draws,))
+    out = torch.empty(draws, dtype=torch.int64, device="cuda")
+    t_scan = _event_ms(lambda: api.sample(n, state, u1, out=out[:1]), reps)
+    t_all = _event_ms(lambda: api.sample(n, state, u, out=out), reps)
+    N = 1 << n
+    res = {"single": {"n": n, "p": p, "draws": draws, "prefix_ms": t_scan, "ms": t_all,
+                      "draws_per_s": draws / ((t_all - t_scan) * 1e-3),
+                      "prefix_GBps": N * 8 / (t_scan * 1e-3) / 1e9,
+                      "prefix_fp64_gflops": 3 * N / (t_scan * 1e-3) / 1e9}}
+    del state, cost, u, out
+    torch.cuda.empty_cache()
+    insts = [gen.protocol_instance("sample-bench", batch_n, batch_k, i) for i in range(batch)]
+    costs, _, _ = api.cost_table_batch(insts)
+    g, b = gen.linear_ramp(batch_p)
+    states, _, _ = api.evolve_batch(batch_n, costs, max(i.m for i in insts), g, b, "c64")
+    ub = gen.device_uniforms("sample-bench-batch", (batch, batch_draws))
+    rts = {}
+
+    def run():
+        rts["rt"] = api.running_time_batch(batch_n, costs, states, ub)
+
+    t_b = _event_ms(run, reps)
+    res["batch"] = {"n": batch_n, "k": batch_k, "p": batch_p, "instances": batch, "draws_each": batch_draws,
+                    "ms": t_b, "draws_per_s": batch * batch_draws / (t_b * 1e-3),
+                    "resolved": int(np.sum(rts["rt"] > 0))}
     return res
