@@ -458,7 +458,7 @@ def main():
     ap.add_argument("--ks", default="9", help="protocol: clause widths (comma separated)")
     ap.add_argument("--ps", default="1,2,4,8,16,32", help="protocol: depths (comma separated)")
     ap.add_argument("--count", type=int, default=2500, help="protocol: satisfiable instances per (k, n)")
-    ap.add_argument("--lr", type=float, default=1e-3, help="protocol: Adam learning rate of the angle training")
+    ap.add_argument("--lr", type=float, default=1e-2, help="protocol: Adam learning rate of the angle training")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

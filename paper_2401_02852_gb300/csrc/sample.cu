@@ -71,6 +71,61 @@ __device__ __forceinline__ double entry_sum(const double2 *st, uint64_t x0, uint
     return s;
 }
 
+// |z|^2 of a complex64 amplitude as a normalised double-float (hi, lo): the
+// squares exact by FMA, their sum by TwoSum.
+__device__ __forceinline__ void prob_df(float2 z, float &hi, float &lo) {
+    const float pr = __fmul_rn(z.x, z.x), er = __fmaf_rn(z.x, z.x, -pr);
+    const float pi = __fmul_rn(z.y, z.y), ei = __fmaf_rn(z.y, z.y, -pi);
+    float s, e;
+    df_two_sum(pr, pi, s, e);
+    df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(er, ei)), hi, lo);
+}
+// (ah, al) + (bh, bl), normalised.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &h, float &l) {
+    float s, e;
+    df_two_sum(ah, bh, s, e);
+    df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(al, bl)), h, l);
+}
+// x > y for normalised double-floats (hi decides unless equal).
+__device__ __forceinline__ bool df_greater(float xh, float xl, float yh, float yl) {
+    return xh > yh || (xh == yh && xl > yl);
+}
+
+// The chosen entry's draw: the first lane x with w(x) > 0 whose inclusive
+// prefix exceeds rest (a warp scan), or when none does (edge, or the
+// remainder at the entry's rounded sum) the last lane with w > 0; -1 when
+// every w is 0.  complex64: probabilities and scan in double-float on the
+// FP32 pipes, rest split into a double-float; complex128: FP64.
+__device__ __forceinline__ int entry_pick(float2 z, bool valid, double rest, bool edge) {
+    const int lane = threadIdx.x & 31;
+    float wh = 0.f, wl = 0.f;
+    if (valid) prob_df(z, wh, wl);
+    float ih = wh, il = wl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float yh = __shfl_up_sync(0xFFFFFFFFu, ih, o), yl = __shfl_up_sync(0xFFFFFFFFu, il, o);
+        if (lane >= o) df_add(ih, il, yh, yl, ih, il);
+    }
+    const float rh = __double2float_rn(rest);
+    const float rl = __double2float_rn(rest - (double)rh);
+    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && wh > 0.f && df_greater(ih, il, rh, rl));
+    const unsigned nz = __ballot_sync(0xFFFFFFFFu, wh > 0.f);
+    return hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : -1);
+}
+__device__ __forceinline__ int entry_pick(double2 z, bool valid, double rest, bool edge) {
+    const int lane = threadIdx.x & 31;
+    const double w = valid ? prob(z) : 0.0;
+    double incl = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && w > 0.0 && incl > rest);
+    const unsigned nz = __ballot_sync(0xFFFFFFFFu, w > 0.0);
+    return hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : -1);
+}
+
 // Entry and group counts of a stored state of 2^ns amplitudes.
 __host__ __device__ __forceinline__ uint64_t entry_count(int ns) {
     return ns > ENTRY_BITS ? 1ull << (ns - ENTRY_BITS) : 1ull;
@@ -214,19 +269,13 @@ __global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, 
     edge = edge || ord(rest) >= ord(Qg[glen - 1]);
     const uint64_t e = warp_search(Qg, glen, rest, edge);
     rest -= e > 0 ? Qg[e - 1] : 0.0;
-    // amplitude within the entry
+    // amplitude within the entry; the chosen entry has a nonzero sum unless
+    // the state's norm is 0 (then x = 0)
     const uint64_t x = ((e0 + e) << ENTRY_BITS) + (uint64_t)lane;
-    const double w = x < N ? prob(st[x]) : 0.0;
-    double incl = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && w > 0.0 && incl > rest);
-    const unsigned nz = __ballot_sync(0xFFFFFFFFu, w > 0.0);
-    // the chosen entry has a nonzero sum (nz != 0) unless the state's norm is 0
-    const int pick = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);
+    V z{};
+    if (x < N) z = st[x];
+    const int pk = entry_pick(z, x < N, rest, edge);
+    const int pick = pk >= 0 ? pk : 0;
     if (lane == 0) {
         const uint64_t found = ((e0 + e) << ENTRY_BITS) + (uint64_t)pick;
         const uint64_t full = (1ull << (ns + (z2 ? 1 : 0))) - 1ull;

@@ -75,7 +75,7 @@ def satisfiable_batch(tag: str, n: int, k: int, count: int, start: int = 0, max_
     return insts, costs
 
 
-def train_fixed_angles(k: int, p: int, n: int = 12, t: int = 100, epochs: int = 100, lr: float = 1e-3,
+def train_fixed_angles(k: int, p: int, n: int = 12, t: int = 100, epochs: int = 100, lr: float = 1e-2,
                        tag: str = "protocol-train", dtype: str = "c128"):
     """Angles for depth p: Adam from beta_i = 0.01, gamma_i = -0.01 on the mean
     p_succ of t random CNF(n, k, r_hat_k) instances (unconditioned draws: an
@@ -181,7 +181,7 @@ def exponents(k: int, points: dict, ps: Sequence[int], ns: Sequence[int]) -> dic
 
 
 def run_protocol(ks: Sequence[int] = (9,), ps: Sequence[int] = (1, 2, 4, 8, 16, 32), ns=range(12, 20),
-                 t: int = 100, epochs: int = 100, lr: float = 1e-3, count: int = 2500, running_times: bool = True,
+                 t: int = 100, epochs: int = 100, lr: float = 1e-2, count: int = 2500, running_times: bool = True,
                  dtype: str = "c64", log=None) -> dict:
     """Training then evaluation for every k in `ks`; a JSON-serialisable dict."""
     ns = list(ns)

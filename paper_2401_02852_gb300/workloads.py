@@ -196,7 +196,7 @@ def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p:
             "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols))}
 
 
-def protocol_workload(ks=(9,), ps=(1, 2, 4, 8, 16, 32), count: int = 2500, lr: float = 1e-3) -> dict:
+def protocol_workload(ks=(9,), ps=(1, 2, 4, 8, 16, 32), count: int = 2500, lr: float = 1e-2) -> dict:
     res = protocol.run_protocol(ks=ks, ps=ps, count=count, lr=lr)
     evolve_s = sum(v["stats"]["evolve_s"] for v in res["by_k"].values())
     amp_layers = sum(v["stats"]["amp_layers"] for v in res["by_k"].values())
