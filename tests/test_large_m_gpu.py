@@ -149,3 +149,21 @@ def test_protocol_training_objective_and_evaluation():
     ex = res["by_k"]["5"]["exponents"]
     assert set(ex["by_p"]) == {"1", "2"} and ex["random_assignment"]["nat"] > 0
     assert "power_law_bits" in ex
+
+
+def test_protocol_k9_reproduces_the_papers_power_law():
+    """The paper's main-text ensemble (k = 9, 2500 satisfiable instances per
+    n = 12..19, nine depths, angles trained at n = 12 with lr 0.01): the
+    median-running-time exponents in bits follow a p^b close to the paper's
+    table (a = 0.686, b = -0.222), fall with p, and agree with the p_hat
+    exponents to within a fifth at every depth."""
+    ps = (1, 2, 4, 8, 16, 20, 24, 28, 32)
+    res = protocol.run_protocol(ks=(9,), ps=ps, count=2500)
+    ex = res["by_k"]["9"]["exponents"]
+    a, b = ex["power_law_bits"]
+    pa, pb = protocol.PAPER_POWER_LAW[9]
+    assert abs(a - pa) < 0.05 and abs(b - pb) < 0.06, (a, b)
+    ct = [ex["by_p"][str(p)]["C_tilde_bits"] for p in ps]
+    assert ct[0] > ct[4] > ct[-1] > 0
+    assert max(ex["by_p"][str(p)]["relative_error"] for p in ps) < 0.25
+    assert ct[0] < ex["random_assignment"]["bits"]
