@@ -21,6 +21,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "pass_common.cuh"
@@ -124,10 +125,13 @@ __device__ __forceinline__ uint32_t reg_off(int r, uint32_t gstride) {
 // A_PHASE then takes the phase term and undoes D_l; A_FUSED (high passes) also
 // undoes layer l-1's butterflies on the same group, in the mapping it ends in
 // and back (with c2 = 1, S2 = 0 and no partials2 it is A_PHASE for a high
-// group).  HROW: row bits of a high pass; FULL: every group bit of the tile is
-// undone here (a compile-time mask, straight-line stages), else the runtime
-// mask.
-template <typename R, bool LOW, int MODE, int NT, int HROW, bool FULL>
+// group).  HROW: row bits of a high pass; FULL: 1 = every group bit of the
+// tile is undone here (a compile-time mask, straight-line stages), 0 = the
+// runtime mask, 2 = (high passes) the runtime mask with every undone bit among
+// the load mapping's register bits, so the pass needs no exchange: the next
+// pair is copied as soon as this one is in registers, and the phase is taken
+// in the load mapping.
+template <typename R, bool LOW, int MODE, int NT, int HROW, int FULL>
 __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const __grid_constant__ AdjArgs<R> a,
                                                                         const __grid_constant__ AdjTab<R, NT> tab) {
     static_assert(!LOW || MODE != A_FUSED, "the low pass never fuses");
@@ -140,7 +144,8 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
     constexpr int LC = LOW ? G::LC_LOW : G::LC_HIGH;
     constexpr int row = LOW ? T : HROW;
     constexpr uint32_t full_mask = ((1u << T) - 1u) & ~(LOW ? 0u : (1u << row) - 1u);
-    const uint32_t active = FULL ? full_mask : a.active;
+    constexpr bool TOP = !LOW && FULL == 2;
+    const uint32_t active = FULL == 1 ? full_mask : a.active;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tp = reinterpret_cast<V *>(smem_raw);
     V *tl = tp + G::TILE_ELEMS;
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
     V *psi = a.psi + (inst << a.n);
     V *lam = a.lam + (inst << a.n);
     const uint8_t *cs = a.cost + (inst << a.n);
-    constexpr int SM = MODE == A_FUSED ? LD : LC;  // store mapping
+    constexpr int SM = (MODE == A_FUSED || TOP) ? LD : LC;  // store mapping
     const uint32_t st_t = elem_offset32(tile_elem<G, SM>(tid, 0), row, a.lo);
     const uint32_t gstride = LOW ? 0u : (1u << a.lo);
     const uint32_t tiles = (uint32_t)a.tiles;
@@ -191,29 +196,37 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
             if (tn < tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
             cp_async_commit();
         };
-        // all of M_l undone on this tile: phase term, then D_l^dagger (mapping LC)
-        auto undo_phase = [&]() {
+        // all of M_l undone on this tile: phase term, then D_l^dagger (registers
+        // in mapping MP)
+        auto undo_phase = [&](auto mp) {
+            constexpr int MP = decltype(mp)::value;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const int cst = sc[tile_elem<G, LC>(tid, r)];
+                const int cst = sc[tile_elem<G, MP>(tid, r)];
                 gterm += (R)cst * (vl[r].x * vp[r].y - vl[r].y * vp[r].x);
                 const V ph = stab[cst];
                 vp[r] = cmul(vp[r], ph);
                 vl[r] = cmul(vl[r], ph);
             }
         };
+        if constexpr (TOP) prefetch();  // the pair is in registers for good
         inv_round<G, LD, T>(vp, vl, active, a.c, a.S, term);
-        if (LOW) {
+        if constexpr (TOP) {
+            if constexpr (MODE == A_FUSED) {
+                undo_phase(std::integral_constant<int, LD>{});
+                inv_round<G, LD, T>(vp, vl, active, a.c2, a.S2, term2);
+            }
+        } else if (LOW) {
             exchange_pair<G, LD, 0>(vp, vl, tp, tl);
             inv_round<G, 0, T>(vp, vl, active, a.c, a.S, term);
             exchange_pair<G, 0, LC>(vp, vl, tp, tl);
             prefetch();
             inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
-            if (PH) undo_phase();
+            if (PH) undo_phase(std::integral_constant<int, LC>{});
         } else if (MODE == A_FUSED) {
             exchange_pair<G, LD, LC>(vp, vl, tp, tl);
             inv_round<G, LC, LD>(vp, vl, active, a.c, a.S, term);
-            undo_phase();
+            undo_phase(std::integral_constant<int, LC>{});
             inv_round<G, LC, LD>(vp, vl, active, a.c2, a.S2, term2);
             exchange_pair<G, LC, LD>(vp, vl, tp, tl);
             prefetch();
@@ -357,14 +370,18 @@ struct AdjKernels {
     using KF = void (*)(AdjArgs<R>, AdjTab<R, MAX_TABLE>);
     using KN = void (*)(AdjArgs<R>, AdjTab<R, 1>);
     static constexpr int W = adj_wrow<R>();
-    KN low = adj_kernel<R, true, A_PLAIN, 1, HIGH_ROW, true>;
-    KF low_phase = adj_kernel<R, true, A_PHASE, MAX_TABLE, HIGH_ROW, true>;
-    // [wide][full]
-    KN high[2][2] = {{adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, false>, adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, true>},
-                     {adj_kernel<R, false, A_PLAIN, 1, W, false>, adj_kernel<R, false, A_PLAIN, 1, W, true>}};
-    KF fused[2][2] = {
-        {adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, false>, adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, true>},
-        {adj_kernel<R, false, A_FUSED, MAX_TABLE, W, false>, adj_kernel<R, false, A_FUSED, MAX_TABLE, W, true>}};
+    KN low = adj_kernel<R, true, A_PLAIN, 1, HIGH_ROW, 1>;
+    KF low_phase = adj_kernel<R, true, A_PHASE, MAX_TABLE, HIGH_ROW, 1>;
+    // [wide][FULL: runtime mask, full, top bits only]
+    KN high[2][3] = {{adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, 0>, adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, 1>,
+                      adj_kernel<R, false, A_PLAIN, 1, HIGH_ROW, 2>},
+                     {adj_kernel<R, false, A_PLAIN, 1, W, 0>, adj_kernel<R, false, A_PLAIN, 1, W, 1>,
+                      adj_kernel<R, false, A_PLAIN, 1, W, 2>}};
+    KF fused[2][3] = {{adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, 0>,
+                       adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, 1>,
+                       adj_kernel<R, false, A_FUSED, MAX_TABLE, HIGH_ROW, 2>},
+                      {adj_kernel<R, false, A_FUSED, MAX_TABLE, W, 0>, adj_kernel<R, false, A_FUSED, MAX_TABLE, W, 1>,
+                       adj_kernel<R, false, A_FUSED, MAX_TABLE, W, 2>}};
 };
 
 template <typename R>
@@ -380,7 +397,7 @@ static int adj_init(AdjKernels<R> **out) {
             e = cudaFuncSetAttribute(ks.low_phase, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)adj_smem<R>(MAX_TABLE - 1));
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+            for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
                 e = cudaFuncSetAttribute(ks.high[w][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)adj_smem<R>(-1));
                 if (e == cudaSuccess)
@@ -474,7 +491,10 @@ static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, cons
             a.active = ((1u << ps.bits) - 1u) << (pl.tile_bits - ps.bits);
             if (ps.row != HIGH_ROW && ps.row != adj_wrow<R>())
                 return set_error(QAOA_ECUDA, "adjoint plan: rows of %d bits", ps.row);
-            const int wide = ps.row != HIGH_ROW ? 1 : 0, full = ps.bits == pl.tile_bits - ps.row ? 1 : 0;
+            // the undone bits are the tile's top ps.bits; the load mapping holds
+            // the top RB in registers
+            const int wide = ps.row != HIGH_ROW ? 1 : 0;
+            const int full = ps.bits == pl.tile_bits - ps.row ? 1 : (ps.bits <= AGeo<R>::RB ? 2 : 0);
             profile_before(K_ADJ_HIGH, stream);
             if (L.mode == A_PLAIN)
                 ks->high[wide][full]<<<dim3(gxa, batch), PT, adj_smem<R>(-1), stream>>>(a, none);

@@ -225,7 +225,11 @@ def test_global_flip_symmetry_of_gpu_state():
 # gradients
 
 
-@pytest.mark.parametrize("n,dtype", [(9, "c128"), (9, "c64"), (14, "c128"), (15, "c64"), (18, "c128"), (18, "c64")])
+# n = 18: the high group is partial with 6 bits (runtime mask); n = 14, 15, 20,
+# 21, 22: the last group's bits are within the load mapping's registers (no
+# exchange); n = 20..22 also run a full 7- or 8-bit group
+@pytest.mark.parametrize("n,dtype", [(9, "c128"), (9, "c64"), (14, "c128"), (15, "c64"), (18, "c128"), (18, "c64"),
+                                     (20, "c64"), (21, "c128"), (21, "c64"), (22, "c64")])
 @pytest.mark.parametrize("sign", [0, 1])
 def test_grad_matches_oracle(n, dtype, sign):
     inst, ref_cost = _sat_inst("gr", n, 5, 8 * n)  # the configured gradient workload family (k = 5, r = 8)
