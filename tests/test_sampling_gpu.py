@@ -181,3 +181,19 @@ def test_sweep_reports_running_times(tmp_path):
         assert "running_time_c_bits" in res["fits"][p]
     again = sweep.run_sweep(ns=(14, 16), ps=(1, 4), seeds=12, out_dir=str(tmp_path), log=None, running_times=True)
     assert again["results"][(16, 4)]["running_times"] == res["results"][(16, 4)]["running_times"]
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_uniforms_outside_the_unit_interval(dtype):
+    """u <= 0 (and NaN) draw the first x of nonzero probability, u >= 1 the
+    last; a state of norm zero draws 0."""
+    n = 13
+    psi = gen.random_state("gpu-edge", n, 0, sparsity=0.5)
+    psi[:37] = 0  # the first entries hold no mass
+    psi[-70:] = 0
+    nz = np.flatnonzero(np.abs(psi.astype(dtype)) > 0)
+    u = np.array([-0.5, -0.0, 0.0, np.nan, 1.0, 1.5, np.inf])
+    got = api.sample(n, torch.from_numpy(psi.astype(dtype)).cuda(), u).cpu().numpy()
+    assert list(got) == [nz[0]] * 4 + [nz[-1]] * 3
+    zero = torch.zeros(1 << n, dtype=torch.complex64 if dtype == np.complex64 else torch.complex128, device="cuda")
+    assert np.all(api.sample(n, zero, np.array([0.0, 0.3, 0.99])).cpu().numpy() == 0)
