@@ -161,6 +161,9 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
             const float4 w = *reinterpret_cast<const float4 *>(&v[r]);
             sd[off(r)] = make_double2((double)w.x + (double)w.y, (double)w.z + (double)w.w);
         }
+    } else if constexpr (is_df<R>()) {  // pairs renormalised between passes
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sp[off(r)] = df_renorm(v[r]);
     } else {
 #pragma unroll
         for (int r = 0; r < NR; ++r) sp[off(r)] = v[r];

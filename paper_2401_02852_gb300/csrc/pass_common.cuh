@@ -186,8 +186,10 @@ __device__ __forceinline__ void df_fast_two_sum(float a, float b, float &s, floa
     e = __fsub_rn(b, __fsub_rn(s, a));
 }
 // x + c y for double-floats (the lo x lo product is below the format's
-// precision and dropped).
-__device__ __forceinline__ dfloat df_axpy(dfloat c, float y_hi, float y_lo, float x_hi, float x_lo) {
+// precision and dropped), left unrenormalised: hi + lo carries the same value
+// with |lo| a few ulp(hi).  The butterflies chain these; the pass renormalises
+// each pair with Fast2Sum before it stores the tile.
+__device__ __forceinline__ dfloat df_axpy_raw(dfloat c, float y_hi, float y_lo, float x_hi, float x_lo) {
     const float p = __fmul_rn(c.hi, y_hi);
     const float pe = __fmaf_rn(c.hi, y_hi, -p);  // c.hi y.hi = p + pe exactly
     float s, se;
@@ -195,8 +197,20 @@ __device__ __forceinline__ dfloat df_axpy(dfloat c, float y_hi, float y_lo, floa
     float lo = __fadd_rn(__fadd_rn(se, pe), x_lo);
     lo = __fmaf_rn(c.hi, y_lo, lo);
     lo = __fmaf_rn(c.lo, y_hi, lo);
+    return dfloat{s, lo};
+}
+// x + c y, renormalised (|lo| <= ulp(hi) / 2).
+__device__ __forceinline__ dfloat df_axpy(dfloat c, float y_hi, float y_lo, float x_hi, float x_lo) {
+    const dfloat t = df_axpy_raw(c, y_hi, y_lo, x_hi, x_lo);
     dfloat r;
-    df_fast_two_sum(s, lo, r.hi, r.lo);
+    df_fast_two_sum(t.hi, t.lo, r.hi, r.lo);
+    return r;
+}
+// A pair renormalised (|hi| >= |lo|, or hi = 0).
+__device__ __forceinline__ float4 df_renorm(float4 v) {
+    float4 r;
+    df_fast_two_sum(v.x, v.y, r.x, r.y);
+    df_fast_two_sum(v.z, v.w, r.z, r.w);
     return r;
 }
 __device__ __forceinline__ dfloat df_neg(dfloat c) { return dfloat{-c.hi, -c.lo}; }
@@ -231,28 +245,29 @@ __device__ __forceinline__ void bfly(V &a, V &b, R A, R B) {
     b = nb;
 }
 
-// The factored butterfly in double-float arithmetic (float4 amplitudes).
+// The factored butterfly in double-float arithmetic (float4 amplitudes; the
+// results are left unrenormalised, see df_axpy_raw).
 template <bool UA>
 __device__ __forceinline__ void bfly(float4 &a, float4 &b, dfloat A, dfloat B) {
     float4 na, nb;
     if (UA) {  // (a + i B b, b + i B a)
         const dfloat nB = df_neg(B);
-        dfloat t = df_axpy(nB, b.z, b.w, a.x, a.y);
+        dfloat t = df_axpy_raw(nB, b.z, b.w, a.x, a.y);
         na.x = t.hi, na.y = t.lo;
-        t = df_axpy(B, b.x, b.y, a.z, a.w);
+        t = df_axpy_raw(B, b.x, b.y, a.z, a.w);
         na.z = t.hi, na.w = t.lo;
-        t = df_axpy(nB, a.z, a.w, b.x, b.y);
+        t = df_axpy_raw(nB, a.z, a.w, b.x, b.y);
         nb.x = t.hi, nb.y = t.lo;
-        t = df_axpy(B, a.x, a.y, b.z, b.w);
+        t = df_axpy_raw(B, a.x, a.y, b.z, b.w);
         nb.z = t.hi, nb.w = t.lo;
     } else {  // (A a + i b, A b + i a)
-        dfloat t = df_axpy(A, a.x, a.y, -b.z, -b.w);
+        dfloat t = df_axpy_raw(A, a.x, a.y, -b.z, -b.w);
         na.x = t.hi, na.y = t.lo;
-        t = df_axpy(A, a.z, a.w, b.x, b.y);
+        t = df_axpy_raw(A, a.z, a.w, b.x, b.y);
         na.z = t.hi, na.w = t.lo;
-        t = df_axpy(A, b.x, b.y, -a.z, -a.w);
+        t = df_axpy_raw(A, b.x, b.y, -a.z, -a.w);
         nb.x = t.hi, nb.y = t.lo;
-        t = df_axpy(A, b.z, b.w, a.x, a.y);
+        t = df_axpy_raw(A, b.z, b.w, a.x, a.y);
         nb.z = t.hi, nb.w = t.lo;
     }
     a = na;
