@@ -65,6 +65,27 @@ __device__ __forceinline__ double entry_sum(const float2 *st, uint64_t x0, uint6
     }
     return (double)hi + (double)lo;  // exact: hi + lo fits a double
 }
+// complex64, from a staged group: entry el's amplitudes 2j, 2j + 1 sit in the
+// float4 at stage[16 el + ((j + el) & 15)] (see entry_scan_kernel); `pairs`
+// of them, summed as above in index order.
+__device__ __forceinline__ double entry_sum_staged(const float4 *stage, uint32_t el, uint32_t pairs) {
+    float hi = 0.f, lo = 0.f;
+    auto add = [&](float zx, float zy) {
+        const float pr = __fmul_rn(zx, zx), er = __fmaf_rn(zx, zx, -pr);
+        const float pi = __fmul_rn(zy, zy), ei = __fmaf_rn(zy, zy, -pi);
+        float s, e;
+        df_two_sum(hi, pr, s, e);
+        lo = __fadd_rn(lo, __fadd_rn(e, er));
+        df_two_sum(s, pi, hi, e);
+        lo = __fadd_rn(lo, __fadd_rn(e, ei));
+    };
+    for (uint32_t j = 0; j < pairs; ++j) {
+        const float4 w = stage[16 * el + ((j + el) & 15)];
+        add(w.x, w.y);
+        add(w.z, w.w);
+    }
+    return (double)hi + (double)lo;
+}
 __device__ __forceinline__ double entry_sum(const double2 *st, uint64_t x0, uint64_t x1) {
     double s = 0.0;
     for (uint64_t x = x0; x < x1; ++x) s += prob(st[x]);
@@ -139,7 +160,14 @@ __host__ __device__ __forceinline__ uint64_t group_count(int ns) {
 // last entry).  The running sums are serial within each warp's 32 entries and
 // offset by the serial sums of the earlier warps' totals, so Q is
 // nondecreasing and Q[e] > Q[e - 1] only where entry e has a nonzero sum.
-template <typename V>
+// With STAGED (complex64 states at 16-byte aligned addresses) the group is
+// first staged in shared memory (dynamic, STAGE_BYTES) with coalesced 16-byte
+// loads, pair j of entry e at float4 slot 16 e + ((j + e) & 15): the loads'
+// quarter-warps write, and the entry reads' quarter-warps read, eight
+// distinct bank quads.
+constexpr int STAGE_PAIRS = 1 << (GROUP_BITS + ENTRY_BITS - 1);
+constexpr size_t STAGE_BYTES = sizeof(float4) * STAGE_PAIRS;
+template <typename V, bool STAGED>
 __global__ void __launch_bounds__(GROUP) entry_scan_kernel(const V *states, int ns, double *Q, double *G) {
     __shared__ double run[GROUP];
     __shared__ double off[GROUP / 32];
@@ -148,7 +176,24 @@ __global__ void __launch_bounds__(GROUP) entry_scan_kernel(const V *states, int 
     const V *st = states + (inst << ns);
     const uint64_t e = ((uint64_t)blockIdx.x << GROUP_BITS) + threadIdx.x;
     double s = 0.0;
-    if (e < ne) {
+    if constexpr (STAGED) {
+        static_assert(sizeof(V) == 8, "complex64 only");
+        extern __shared__ float4 stage[];
+        const uint64_t gx0 = (uint64_t)blockIdx.x << (GROUP_BITS + ENTRY_BITS);  // first amplitude (even)
+        const uint64_t left = (N - gx0) / 2;  // N even: ns >= 1
+        const uint32_t np = left < (uint64_t)STAGE_PAIRS ? (uint32_t)left : (uint32_t)STAGE_PAIRS;
+        const float4 *src = reinterpret_cast<const float4 *>(st + gx0);
+        for (uint32_t q = threadIdx.x; q < np; q += GROUP) {
+            const uint32_t qe = q >> (ENTRY_BITS - 1), qj = q & 15u;
+            stage[16 * qe + ((qj + qe) & 15u)] = src[q];
+        }
+        __syncthreads();
+        if (e < ne) {
+            const uint32_t el = threadIdx.x;
+            const uint32_t pairs = np > 16 * el ? (np - 16 * el < 16u ? np - 16 * el : 16u) : 0u;
+            s = entry_sum_staged(stage, el, pairs);
+        }
+    } else if (e < ne) {
         const uint64_t x0 = e << ENTRY_BITS, x1 = x0 + 32 < N ? x0 + 32 : N;
         s = entry_sum(st, x0, x1);
     }
@@ -326,12 +371,20 @@ static int sample_impl(int batch, int n, const uint8_t *d_costs, const void *d_s
     profile_before(K_SAMPLE, stream);
     if (dtype == QAOA_C64) {
         const float2 *st = reinterpret_cast<const float2 *>(d_states);
-        entry_scan_kernel<float2><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+        if ((reinterpret_cast<uintptr_t>(d_states) & 15u) == 0) {
+            static const cudaError_t attr = cudaFuncSetAttribute(
+                entry_scan_kernel<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGE_BYTES);
+            if (attr != cudaSuccess) return cuda_error(attr, "entry scan shared memory");
+            entry_scan_kernel<float2, true><<<dim3((unsigned)ng, batch), GROUP, STAGE_BYTES, stream>>>(st, ns, d_q,
+                                                                                                      d_pre);
+        } else {
+            entry_scan_kernel<float2, false><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+        }
         block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, ng);
         draw_kernel<float2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_pre, k, d_u, xs);
     } else {
         const double2 *st = reinterpret_cast<const double2 *>(d_states);
-        entry_scan_kernel<double2><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+        entry_scan_kernel<double2, false><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
         block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, ng);
         draw_kernel<double2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_pre, k, d_u, xs);
     }

@@ -197,3 +197,17 @@ def test_uniforms_outside_the_unit_interval(dtype):
     assert list(got) == [nz[0]] * 4 + [nz[-1]] * 3
     zero = torch.zeros(1 << n, dtype=torch.complex64 if dtype == np.complex64 else torch.complex128, device="cuda")
     assert np.all(api.sample(n, zero, np.array([0.0, 0.3, 0.99])).cpu().numpy() == 0)
+
+
+def test_staged_and_unstaged_prefix_agree():
+    """A complex64 state at an address that is not 16-byte aligned takes the
+    unstaged entry sums; both orders of work give the same draws."""
+    n = 15
+    psi = gen.random_state("gpu-align", n, 0, sparsity=0.3).astype(np.complex64)
+    buf = torch.zeros((1 << n) + 1, dtype=torch.complex64, device="cuda")
+    buf[1:] = torch.from_numpy(psi).cuda()
+    aligned = torch.from_numpy(psi).cuda()
+    shifted = buf[1:]
+    assert shifted.data_ptr() % 16 == 8
+    u = gen.uniforms("gpu-align", 5000, 0)
+    assert torch.equal(api.sample(n, aligned, u), api.sample(n, shifted, u))
