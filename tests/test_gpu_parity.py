@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here; each follows from the rounding of the arithmetic):
   * cost table, solution count, max C: bit-exact;
   * complex128 path: p_succ relative error <= 1e-10, amplitudes within 1e-13;
   * complex64 path: p_succ relative error <= 1e-4, norm within 1e-5, amplitudes
