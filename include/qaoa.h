@@ -192,10 +192,11 @@ int qaoa_success_prob_noalloc(int n, const uint8_t *d_cost, const void *d_state,
  * that satisfies it).  The caller supplies the randomness: one uniform u_j in
  * [0, 1) per draw, device float64 [k] (per instance [batch][k]).  Draw j is
  *   x_j = min { x : F(x) > u_j F_total },   F(x) = sum_{y <= x} |psi(y)|^2
- * (inverse CDF in index order; sums of 32 probabilities formed in FP64, or
- * for complex64 in double-float arithmetic from exact squares, then FP64
- * prefixes, so it differs from a sequential FP64 scan only for u_j within
- * rounding of a step of F).  An x of probability zero is never drawn; a u_j
+ * (inverse CDF in index order; within each block of 2^13 amplitudes the
+ * probabilities are integer weights on a binary scale, about 2^-44 of the
+ * block's largest probability, summed exactly; the block totals are summed
+ * in FP64; so it differs from a sequential FP64 scan only for u_j within
+ * about 2^-40 F_total of a step of F).  An x of probability zero is never drawn; a u_j
  * <= 0 yields the first and a u_j >= 1 the last x of nonzero probability; a
  * state of norm zero draws 0.  With QAOA_Z2_HALF the state and table are the
  * halved ones (the x with bit n-1 clear, psi(not x) = psi(x)) and draws cover

@@ -4,25 +4,25 @@
 // including the first one that satisfies it).
 //
 // Inverse-CDF sampling with caller-supplied uniforms u_j in [0, 1): draw j is
-// the smallest x with F(x) > u_j F_total, F(x) = sum_{y <= x} |psi(y)|^2.  The
-// sums are formed in FP64 (complex64 entry sums in double-float arithmetic
-// with exact squares, about 2^-44 relative), so the result differs from a
-// sequential FP64 scan only through rounding, i.e. only for a u_j within
-// rounding of a step of F.
+// the smallest x with F(x) > u_j F_total, F(x) = sum_{y <= x} |psi(y)|^2.
 //
-// Two-level prefix.  An entry is 32 consecutive amplitudes, a group 256
-// entries (2^13 amplitudes).
-//   1. entry_scan_kernel: one CTA per group: each thread sums one entry in
-//      index order (complex64: on the FP32 pipes, see entry_sum), then the CTA
-//      forms the inclusive prefix Q of its 256 entry sums (fixed order) and
-//      writes the group total;
-//   2. block_prefix_kernel: inclusive prefix P of the group totals, fixed order;
-//   3. draw_kernel: one warp per draw: 32-way searches over P and over the
-//      group's Q, then one FP64 warp scan over the chosen entry's 32
-//      amplitudes.
-// GB300's FP64 pipe is narrow, so a draw forms only those 32 probabilities in
-// FP64; the searches compare the stored nonnegative sums as integers (the bit
-// patterns of doubles >= +0 order as the values do).
+// Two-level prefix: an entry is 32 amplitudes, a group 256 entries (2^13
+// amplitudes).  Within a group the probabilities are integer weights on a
+// per-group binary scale (see weight()), so the entry prefix Q of a group is
+// exact and a draw's scan of its entry re-forms the same integers: the entry
+// and amplitude levels agree to the unit, in any summation order.  Only the
+// group totals are FP64, and their prefix P is formed serially (fixed order).
+//   1. entry_scan_kernel: one CTA per group: the group's largest probability
+//      sets its scale E_g; each thread sums its entry's weights; an exact
+//      warp/block scan gives Q; the group total goes to FP64;
+//   2. block_prefix_kernel: inclusive prefix P of the group totals;
+//   3. draw_kernel: one warp per draw: a 32-way search over P (doubles >= +0
+//      compared as integers), the remainder in the group's units, a 32-way
+//      search over Q, then an integer warp scan over the entry's 32 weights.
+// The draws differ from a sequential FP64 scan of the probabilities only for
+// a u_j within about 2^-40 of a step of F (the weights' quantisation).
+// GB300's FP64 pipe is narrow: apart from a few operations per draw and per
+// group, the sampler runs on the FP32 pipes and the integer ALUs.
 // With QAOA_Z2_HALF the stored half holds the x with bit n-1 clear and
 // |psi(not x)| = |psi(x)| (Sec. 2.2's global flip): t = u 2 F_half picks the
 // stored x (t < F_half) or the complement of the x drawn at t - F_half.
@@ -40,112 +40,7 @@ constexpr int GROUP_BITS = 8;    // log2 entries per group
 constexpr int GROUP = 1 << GROUP_BITS;
 constexpr int PREFIX_PT = 1024;  // threads of the group-prefix kernel
 constexpr int DRAW_WARPS = 8;    // draws per CTA of the draw kernel
-
-template <typename V>
-__device__ __forceinline__ double prob(const V &z) {
-    const double re = (double)z.x, im = (double)z.y;
-    return re * re + im * im;
-}
-
-// Sum of |psi(x)|^2 over x in [x0, x1), in index order.  complex64: the
-// squares are exact as p + e (FMA form of Dekker's TwoProduct), each p is
-// added to a double-float accumulator with Knuth's TwoSum and the rounding
-// errors collect in its low word, all on the FP32 pipes; complex128: FP64.
-__device__ __forceinline__ double entry_sum(const float2 *st, uint64_t x0, uint64_t x1) {
-    float hi = 0.f, lo = 0.f;
-    for (uint64_t x = x0; x < x1; ++x) {
-        const float2 z = st[x];
-        const float pr = __fmul_rn(z.x, z.x), er = __fmaf_rn(z.x, z.x, -pr);
-        const float pi = __fmul_rn(z.y, z.y), ei = __fmaf_rn(z.y, z.y, -pi);
-        float s, e;
-        df_two_sum(hi, pr, s, e);
-        lo = __fadd_rn(lo, __fadd_rn(e, er));
-        df_two_sum(s, pi, hi, e);
-        lo = __fadd_rn(lo, __fadd_rn(e, ei));
-    }
-    return (double)hi + (double)lo;  // exact: hi + lo fits a double
-}
-// complex64, from a staged group: entry el's amplitudes 2j, 2j + 1 sit in the
-// float4 at stage[16 el + ((j + el) & 15)] (see entry_scan_kernel); `pairs`
-// of them, summed as above in index order.
-__device__ __forceinline__ double entry_sum_staged(const float4 *stage, uint32_t el, uint32_t pairs) {
-    float hi = 0.f, lo = 0.f;
-    auto add = [&](float zx, float zy) {
-        const float pr = __fmul_rn(zx, zx), er = __fmaf_rn(zx, zx, -pr);
-        const float pi = __fmul_rn(zy, zy), ei = __fmaf_rn(zy, zy, -pi);
-        float s, e;
-        df_two_sum(hi, pr, s, e);
-        lo = __fadd_rn(lo, __fadd_rn(e, er));
-        df_two_sum(s, pi, hi, e);
-        lo = __fadd_rn(lo, __fadd_rn(e, ei));
-    };
-    for (uint32_t j = 0; j < pairs; ++j) {
-        const float4 w = stage[16 * el + ((j + el) & 15)];
-        add(w.x, w.y);
-        add(w.z, w.w);
-    }
-    return (double)hi + (double)lo;
-}
-__device__ __forceinline__ double entry_sum(const double2 *st, uint64_t x0, uint64_t x1) {
-    double s = 0.0;
-    for (uint64_t x = x0; x < x1; ++x) s += prob(st[x]);
-    return s;
-}
-
-// |z|^2 of a complex64 amplitude as a normalised double-float (hi, lo): the
-// squares exact by FMA, their sum by TwoSum.
-__device__ __forceinline__ void prob_df(float2 z, float &hi, float &lo) {
-    const float pr = __fmul_rn(z.x, z.x), er = __fmaf_rn(z.x, z.x, -pr);
-    const float pi = __fmul_rn(z.y, z.y), ei = __fmaf_rn(z.y, z.y, -pi);
-    float s, e;
-    df_two_sum(pr, pi, s, e);
-    df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(er, ei)), hi, lo);
-}
-// (ah, al) + (bh, bl), normalised.
-__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &h, float &l) {
-    float s, e;
-    df_two_sum(ah, bh, s, e);
-    df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(al, bl)), h, l);
-}
-// x > y for normalised double-floats (hi decides unless equal).
-__device__ __forceinline__ bool df_greater(float xh, float xl, float yh, float yl) {
-    return xh > yh || (xh == yh && xl > yl);
-}
-
-// The chosen entry's draw: the first lane x with w(x) > 0 whose inclusive
-// prefix exceeds rest (a warp scan), or when none does (edge, or the
-// remainder at the entry's rounded sum) the last lane with w > 0; -1 when
-// every w is 0.  complex64: probabilities and scan in double-float on the
-// FP32 pipes, rest split into a double-float; complex128: FP64.
-__device__ __forceinline__ int entry_pick(float2 z, bool valid, double rest, bool edge) {
-    const int lane = threadIdx.x & 31;
-    float wh = 0.f, wl = 0.f;
-    if (valid) prob_df(z, wh, wl);
-    float ih = wh, il = wl;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const float yh = __shfl_up_sync(0xFFFFFFFFu, ih, o), yl = __shfl_up_sync(0xFFFFFFFFu, il, o);
-        if (lane >= o) df_add(ih, il, yh, yl, ih, il);
-    }
-    const float rh = __double2float_rn(rest);
-    const float rl = __double2float_rn(rest - (double)rh);
-    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && wh > 0.f && df_greater(ih, il, rh, rl));
-    const unsigned nz = __ballot_sync(0xFFFFFFFFu, wh > 0.f);
-    return hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : -1);
-}
-__device__ __forceinline__ int entry_pick(double2 z, bool valid, double rest, bool edge) {
-    const int lane = threadIdx.x & 31;
-    const double w = valid ? prob(z) : 0.0;
-    double incl = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && w > 0.0 && incl > rest);
-    const unsigned nz = __ballot_sync(0xFFFFFFFFu, w > 0.0);
-    return hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : -1);
-}
+constexpr int W_TOP = 44;        // a group's largest probability scales into [2^44, 2^46)
 
 // Entry and group counts of a stored state of 2^ns amplitudes.
 __host__ __device__ __forceinline__ uint64_t entry_count(int ns) {
@@ -155,71 +50,130 @@ __host__ __device__ __forceinline__ uint64_t group_count(int ns) {
     return (entry_count(ns) + GROUP - 1) >> GROUP_BITS;
 }
 
-// Group g = blockIdx.x of instance blockIdx.y: Q[e] = sum of the entry sums of
-// the group up to entry e (inclusive), G[g] = the group's total (= Q at its
-// last entry).  The running sums are serial within each warp's 32 entries and
-// offset by the serial sums of the earlier warps' totals, so Q is
-// nondecreasing and Q[e] > Q[e - 1] only where entry e has a nonzero sum.
-// With STAGED (complex64 states at 16-byte aligned addresses) the group is
-// first staged in shared memory (dynamic, STAGE_BYTES) with coalesced 16-byte
-// loads, pair j of entry e at float4 slot 16 e + ((j + e) & 15): the loads'
-// quarter-warps write, and the entry reads' quarter-warps read, eight
-// distinct bank quads.
+// ---- fixed-point weights ------------------------------------------------------
+// In group g every probability is taken as the integer
+//   W(x) = |psi(x)|^2 2^E_g, to about 2^-44 of the group's largest one,
+// with E_g even and set by that largest probability (it lands in
+// [2^44, 2^46)), so an entry (32 amplitudes) sums below 2^51 and a group below
+// 2^59.  Integer sums are exact in any order: the entry prefix of a group is
+// the exact running sum of its entries' W, and a draw re-forms the same W of
+// its entry's 32 amplitudes, so the levels agree to the unit.  complex64:
+// the components are scaled by 2^(E/2) (exact), squared exactly as p + e (the
+// FMA form of Dekker's TwoProduct), p_re + p_im split by Knuth's TwoSum, and
+// W = trunc(s) + trunc(rest of the sum): FP32 and integer operations.
+// complex128: |psi|^2 2^E in FP64, truncated.
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }       // e in [-126, 127]
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// trunc(f) for |f| < 2^63 from the float's bits with integer operations (the
+// float-to-int64 conversion instruction runs on the FP64 pipe).
+__device__ __forceinline__ long long trunc_ll(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xFFu);
+    const uint32_t mant = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+    const int sh = (ex ? ex : 1) - 150;  // |f| = mant 2^sh
+    const long long v = sh >= 0 ? (long long)((unsigned long long)mant << sh) : (sh > -24 ? (long long)(mant >> -sh) : 0);
+    return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ long long weight(float2 z, int E) {
+    const float sc = pow2f(E / 2);
+    const float re = __fmul_rn(z.x, sc), im = __fmul_rn(z.y, sc);
+    const float pr = __fmul_rn(re, re), er = __fmaf_rn(re, re, -pr);
+    const float pi = __fmul_rn(im, im), ei = __fmaf_rn(im, im, -pi);
+    float s, e;
+    df_two_sum(pr, pi, s, e);
+    const float t = __fadd_rn(__fadd_rn(e, er), ei);
+    return trunc_ll(s) + trunc_ll(t);
+}
+__device__ __forceinline__ long long weight(double2 z, int E) {
+    const double w = z.x * z.x + z.y * z.y;
+    return __double2ll_rz(w * pow2d(E));
+}
+// |psi(x)|^2 as a float (to choose E) and the exponent that scales a maximum m.
+__device__ __forceinline__ float prob_f(float2 z) { return z.x * z.x + z.y * z.y; }
+__device__ __forceinline__ float prob_f(double2 z) { return (float)(z.x * z.x + z.y * z.y); }
+__device__ __forceinline__ int scale_exp(float m) {
+    if (!(m > 0.f)) return 0;
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 127;  // m in [2^e, 2^(e+1)) (normal m)
+    int E = W_TOP - (e > -127 ? e : -126);
+    E &= ~1;  // even: the components take 2^(E/2)
+    return E < -200 ? -200 : (E > 200 ? 200 : E);
+}
+
+// Group g = blockIdx.x of instance blockIdx.y: E[g], the inclusive prefix Q
+// (int64) of its entries' weights, and the group total G[g] = Q_last 2^-E_g
+// in FP64.  With STAGED (complex64 states at 16-byte aligned addresses) the
+// group is first staged in shared memory (dynamic, STAGE_BYTES) with
+// coalesced 16-byte loads, pair j of entry e at float4 slot
+// 16 e + ((j + e) & 15): the loads' and the entry reads' quarter-warps hit
+// eight distinct bank quads.
 constexpr int STAGE_PAIRS = 1 << (GROUP_BITS + ENTRY_BITS - 1);
 constexpr size_t STAGE_BYTES = sizeof(float4) * STAGE_PAIRS;
 template <typename V, bool STAGED>
-__global__ void __launch_bounds__(GROUP) entry_scan_kernel(const V *states, int ns, double *Q, double *G) {
-    __shared__ double run[GROUP];
-    __shared__ double off[GROUP / 32];
+__global__ void __launch_bounds__(GROUP) entry_scan_kernel(const V *states, int ns, long long *Q, int *Eg,
+                                                           double *G) {
+    __shared__ long long wsum[GROUP / 32];
+    __shared__ unsigned int smax;
     const uint64_t N = 1ull << ns, ne = entry_count(ns), ng = group_count(ns);
     const uint64_t inst = blockIdx.y;
     const V *st = states + (inst << ns);
-    const uint64_t e = ((uint64_t)blockIdx.x << GROUP_BITS) + threadIdx.x;
-    double s = 0.0;
+    const uint32_t el = threadIdx.x;
+    const uint64_t e = ((uint64_t)blockIdx.x << GROUP_BITS) + el;
+    const uint64_t x0 = e << ENTRY_BITS;
+    const uint32_t cnt = e < ne ? (uint32_t)(N - x0 < 32 ? N - x0 : 32) : 0u;  // amplitudes of this entry
+    if (el == 0) smax = 0u;
+    const float4 *stage = nullptr;
     if constexpr (STAGED) {
         static_assert(sizeof(V) == 8, "complex64 only");
-        extern __shared__ float4 stage[];
+        extern __shared__ float4 stage_buf[];
         const uint64_t gx0 = (uint64_t)blockIdx.x << (GROUP_BITS + ENTRY_BITS);  // first amplitude (even)
         const uint64_t left = (N - gx0) / 2;  // N even: ns >= 1
         const uint32_t np = left < (uint64_t)STAGE_PAIRS ? (uint32_t)left : (uint32_t)STAGE_PAIRS;
         const float4 *src = reinterpret_cast<const float4 *>(st + gx0);
         for (uint32_t q = threadIdx.x; q < np; q += GROUP) {
             const uint32_t qe = q >> (ENTRY_BITS - 1), qj = q & 15u;
-            stage[16 * qe + ((qj + qe) & 15u)] = src[q];
+            stage_buf[16 * qe + ((qj + qe) & 15u)] = src[q];
         }
-        __syncthreads();
-        if (e < ne) {
-            const uint32_t el = threadIdx.x;
-            const uint32_t pairs = np > 16 * el ? (np - 16 * el < 16u ? np - 16 * el : 16u) : 0u;
-            s = entry_sum_staged(stage, el, pairs);
-        }
-    } else if (e < ne) {
-        const uint64_t x0 = e << ENTRY_BITS, x1 = x0 + 32 < N ? x0 + 32 : N;
-        s = entry_sum(st, x0, x1);
+        stage = stage_buf;
     }
-    run[threadIdx.x] = s;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {  // serial running sums of this warp's entries
-        double r = 0.0;
-        for (int i = 0; i < 32; ++i) {
-            r += run[32 * w + i];
-            run[32 * w + i] = r;
+    // amplitude i (< cnt) of this thread's entry
+    auto amp = [&](uint32_t i) -> V {
+        if constexpr (STAGED) {
+            const float4 w = stage[16 * el + (((i >> 1) + el) & 15u)];
+            return (i & 1u) ? make_float2(w.z, w.w) : make_float2(w.x, w.y);
+        } else {
+            return st[x0 + i];
         }
-    }
+    };
+    __syncthreads();  // staged tile and smax
+    float m = 0.f;
+    for (uint32_t i = 0; i < cnt; ++i) m = fmaxf(m, prob_f(amp(i)));
+    atomicMax(&smax, __float_as_uint(m));  // nonnegative floats order as their bits
     __syncthreads();
-    if (threadIdx.x == 0) {  // warp totals -> offsets, in order
-        double r = 0.0;
-        for (int i = 0; i < GROUP / 32; ++i) {
-            off[i] = r;
-            r = r + run[32 * i + 31];
-        }
+    const int E = scale_exp(__uint_as_float(smax));
+    long long wv = 0;
+    for (uint32_t i = 0; i < cnt; ++i) wv += weight(amp(i), E);
+    // inclusive scan over the group's 256 entries (exact integer sums)
+    const int lane = el & 31, w = el >> 5;
+    long long incl = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
     }
+    if (lane == 31) wsum[w] = incl;
     __syncthreads();
-    const double q = off[w] + run[threadIdx.x];
-    if (e < ne) Q[inst * ne + e] = q;
-    const uint64_t left = ne - ((uint64_t)blockIdx.x << GROUP_BITS);  // entries of this group
-    if ((uint64_t)threadIdx.x == (left < (uint64_t)GROUP ? left : (uint64_t)GROUP) - 1) G[inst * ng + blockIdx.x] = q;
+    long long off = 0;
+    for (int i = 0; i < w; ++i) off += wsum[i];
+    incl += off;
+    if (e < ne) Q[inst * ne + e] = incl;
+    const uint64_t gl = ne - ((uint64_t)blockIdx.x << GROUP_BITS);  // entries of this group
+    if ((uint64_t)el == (gl < (uint64_t)GROUP ? gl : (uint64_t)GROUP) - 1) {
+        G[inst * ng + blockIdx.x] = (double)incl * pow2d(-E);
+        Eg[inst * ng + blockIdx.x] = E;
+    }
 }
 
 // In place, per instance (one CTA each): sums[b] <- sums[0] + ... + sums[b].
@@ -254,24 +208,24 @@ __global__ void __launch_bounds__(PREFIX_PT) block_prefix_kernel(double *sums, u
 }
 
 // Doubles >= +0 compare as their bit patterns do (as signed 64-bit integers),
-// which keeps the searches off the FP64 pipe.
+// which keeps the group search off the FP64 pipe.
 __device__ __forceinline__ long long ord(double v) { return __double_as_longlong(v); }
 
-// Smallest i in [0, len) with A[i] > key (A nondecreasing, A[len - 1] > key),
-// or with A[i] >= A[len - 1] when `edge`; a 32-way search by the whole warp.
-// Every A[i] and key are >= +0.
-__device__ __forceinline__ uint64_t warp_search(const double *A, uint64_t len, double key, bool edge) {
-    const int lane = threadIdx.x & 31;
-    const long long kb = ord(edge ? A[len - 1] : key);
-    uint64_t lo = 0, hi = len;  // the answer is in [lo, hi)
+// Smallest i in [0, len) with key(A[i]) > kb (A nondecreasing, the last one
+// qualifies), or >= kb when `ge`; a 32-way search by the whole warp
+// (len < 2^31: at most 2^19 groups, 256 entries).
+template <typename T, typename K>
+__device__ __forceinline__ uint32_t warp_search(const T *A, uint32_t len, long long kb, bool ge, K key) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t lo = 0, hi = len;  // the answer is in [lo, hi)
     while (hi - lo > 1) {
-        const uint64_t stride = (hi - lo + 31) / 32;
-        uint64_t i = lo + (uint64_t)(lane + 1) * stride - 1;
+        const uint32_t stride = (hi - lo + 31) / 32;
+        uint32_t i = lo + (lane + 1) * stride - 1;
         if (i > hi - 1) i = hi - 1;
-        const long long v = ord(A[i]);
-        const unsigned ok = __ballot_sync(0xFFFFFFFFu, edge ? v >= kb : v > kb);
-        const uint64_t f = (uint64_t)(__ffs(ok) - 1);  // A[hi - 1] qualifies, so ok != 0
-        const uint64_t nlo = lo + f * stride;
+        const long long v = key(A[i]);
+        const unsigned ok = __ballot_sync(0xFFFFFFFFu, ge ? v >= kb : v > kb);
+        const uint32_t f = (uint32_t)(__ffs(ok) - 1);  // A[hi - 1] qualifies, so ok != 0
+        const uint32_t nlo = lo + f * stride;
         hi = nlo + stride < hi ? nlo + stride : hi;
         lo = nlo;
     }
@@ -279,14 +233,16 @@ __device__ __forceinline__ uint64_t warp_search(const double *A, uint64_t len, d
 }
 
 // One warp per draw j of instance blockIdx.y: x_j = min { x : F(x) > t } with
-// t = u_j F_total; an x of probability zero never wins.  When rounding leaves
-// no x qualifying at some level (t at F_total, or the remainder at a group's or
-// an entry's rounded total) the last x of nonzero probability under the
-// chosen group and entry is taken.
+// t = u_j F_total.  The group comes from the FP64 prefix P; within it the
+// remainder becomes the group's integer units and the rest is exact: the
+// entry from Q, then the first amplitude whose running weight passes it.
+// When t is at F_total, or the remainder at or past the group's integer total
+// (the FP64 group totals are rounded), the last x of nonzero weight of the
+// group is taken; a state of norm zero draws 0.
 template <typename V>
-__global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, int ns, int z2, const double *Q,
-                                                                 const double *P, int k, const double *u,
-                                                                 uint64_t *xs) {
+__global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, int ns, int z2, const long long *Q,
+                                                                 const int *Eg, const double *P, int k,
+                                                                 const double *u, uint64_t *xs) {
     const int lane = threadIdx.x & 31;
     const uint64_t j = (uint64_t)blockIdx.x * DRAW_WARPS + (threadIdx.x >> 5);
     if (j >= (uint64_t)k) return;  // whole warps leave together
@@ -303,24 +259,37 @@ __global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, 
         flip = true;
         t -= total;
     }
-    // group (t, the sums and every remainder below are >= +0)
+    // group (t and the sums are >= +0)
     bool edge = ord(t) >= ord(total);
-    const uint64_t g = warp_search(Pi, ng, t, edge);
-    double rest = t - (g > 0 ? Pi[g - 1] : 0.0);
-    // entry within the group
+    auto dkey = [](double v) { return ord(v); };
+    const uint64_t g = warp_search(Pi, (uint32_t)ng, ord(edge ? total : t), edge, dkey);
+    const int E = Eg[inst * ng + g];
+    // the remainder in the group's integer units
     const uint64_t e0 = g << GROUP_BITS;
     const uint64_t glen = ne - e0 < (uint64_t)GROUP ? ne - e0 : (uint64_t)GROUP;
-    const double *Qg = Q + inst * ne + e0;
-    edge = edge || ord(rest) >= ord(Qg[glen - 1]);
-    const uint64_t e = warp_search(Qg, glen, rest, edge);
-    rest -= e > 0 ? Qg[e - 1] : 0.0;
-    // amplitude within the entry; the chosen entry has a nonzero sum unless
-    // the state's norm is 0 (then x = 0)
+    const long long *Qg = Q + inst * ne + e0;
+    const long long Ig = Qg[glen - 1];
+    long long R = 0;
+    if (!edge) {
+        const double rest = (t - (g > 0 ? Pi[g - 1] : 0.0)) * pow2d(E);  // >= 0, exact scaling
+        R = rest < 9.0e18 ? __double2ll_rz(rest) : Ig;
+        edge = R >= Ig;
+    }
+    auto ikey = [](long long v) { return v; };
+    const uint64_t e = warp_search(Qg, (uint32_t)glen, edge ? Ig : R, edge, ikey);
+    R -= e > 0 ? Qg[e - 1] : 0;
+    // amplitude within the entry: exact integer running weights
     const uint64_t x = ((e0 + e) << ENTRY_BITS) + (uint64_t)lane;
-    V z{};
-    if (x < N) z = st[x];
-    const int pk = entry_pick(z, x < N, rest, edge);
-    const int pick = pk >= 0 ? pk : 0;
+    const long long wv = x < N ? weight(st[x], E) : 0;
+    long long incl = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned hit = __ballot_sync(0xFFFFFFFFu, !edge && incl > R);
+    const unsigned nz = __ballot_sync(0xFFFFFFFFu, wv > 0);
+    const int pick = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);
     if (lane == 0) {
         const uint64_t found = ((e0 + e) << ENTRY_BITS) + (uint64_t)pick;
         const uint64_t full = (1ull << (ns + (z2 ? 1 : 0))) - 1ull;
@@ -355,16 +324,19 @@ static int sample_impl(int batch, int n, const uint8_t *d_costs, const void *d_s
     if (!running_time && !d_x) return set_error(QAOA_EINVAL, "nowhere to put the draws");
     const int ns = z2 ? n - 1 : n;  // index bits of the stored state and of its table
     const uint64_t ne = entry_count(ns), ng = group_count(ns);
-    const size_t qb = sizeof(double) * ne * (size_t)batch;
-    const size_t pre = qb + ((sizeof(double) * ng * (size_t)batch + 255) & ~(size_t)255);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t qb = al(sizeof(long long) * ne * (size_t)batch);
+    const size_t eb = al(sizeof(int) * ng * (size_t)batch);
+    const size_t pre = qb + eb + al(sizeof(double) * ng * (size_t)batch);
     const size_t xb = d_x ? 0 : sizeof(uint64_t) * (size_t)k * batch;
     const size_t fb = sizeof(int) * (size_t)batch;
     Scratch *sc = nullptr;
     int rc = scratch_for(stream, pre + xb + fb + 64, fb + 64, &sc);
     if (rc) return rc;
     char *dev = reinterpret_cast<char *>(sc->dev);
-    double *d_q = reinterpret_cast<double *>(dev);
-    double *d_pre = reinterpret_cast<double *>(dev + qb);
+    long long *d_q = reinterpret_cast<long long *>(dev);
+    int *d_e = reinterpret_cast<int *>(dev + qb);
+    double *d_pre = reinterpret_cast<double *>(dev + qb + eb);
     uint64_t *xs = d_x ? d_x : reinterpret_cast<uint64_t *>(dev + pre);
     int *d_first = reinterpret_cast<int *>(dev + pre + xb);
     const dim3 draw_grid((unsigned)((k + DRAW_WARPS - 1) / DRAW_WARPS), batch);
@@ -376,17 +348,19 @@ static int sample_impl(int batch, int n, const uint8_t *d_costs, const void *d_s
                 entry_scan_kernel<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGE_BYTES);
             if (attr != cudaSuccess) return cuda_error(attr, "entry scan shared memory");
             entry_scan_kernel<float2, true><<<dim3((unsigned)ng, batch), GROUP, STAGE_BYTES, stream>>>(st, ns, d_q,
-                                                                                                      d_pre);
+                                                                                                      d_e, d_pre);
         } else {
-            entry_scan_kernel<float2, false><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+            entry_scan_kernel<float2, false><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_e, d_pre);
         }
         block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, ng);
-        draw_kernel<float2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_pre, k, d_u, xs);
+        draw_kernel<float2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_e, d_pre, k, d_u,
+                                                                       xs);
     } else {
         const double2 *st = reinterpret_cast<const double2 *>(d_states);
-        entry_scan_kernel<double2, false><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_pre);
+        entry_scan_kernel<double2, false><<<dim3((unsigned)ng, batch), GROUP, 0, stream>>>(st, ns, d_q, d_e, d_pre);
         block_prefix_kernel<<<batch, PREFIX_PT, 0, stream>>>(d_pre, ng);
-        draw_kernel<double2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_pre, k, d_u, xs);
+        draw_kernel<double2><<<draw_grid, DRAW_WARPS * 32, 0, stream>>>(st, ns, z2 ? 1 : 0, d_q, d_e, d_pre, k, d_u,
+                                                                        xs);
     }
     rc = profile_after(K_SAMPLE, stream);
     if (rc || !running_time) return rc;
