@@ -50,18 +50,34 @@ def random_assignment_exponent(k: int) -> float:
     return 2.0 ** (1 - k) * gen.threshold_density(k)
 
 
-def satisfiable_batch(tag: str, n: int, k: int, count: int, start: int = 0, max_attempts: int = 10_000):
+def _workers() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def first_attempts(tag: str, n: int, k: int, count: int, start: int = 0) -> list:
+    """Attempt 0 of instances start .. start + count - 1 (drawn in parallel:
+    numpy's draws release the GIL)."""
+    with ThreadPoolExecutor(_workers()) as pool:
+        return list(pool.map(lambda i: gen.protocol_instance(tag, n, k, start + i, 0), range(count)))
+
+
+def satisfiable_batch(tag: str, n: int, k: int, count: int, start: int = 0, max_attempts: int = 10_000,
+                      first: Optional[list] = None):
     """Instances start .. start + count - 1 of CNF(n, k, r_hat_k), each its first
-    satisfiable attempt, and their cost tables (uint8 [count, 2^n], device)."""
+    satisfiable attempt, and their cost tables (uint8 [count, 2^n], device).
+    `first`: their attempts 0 when already drawn (``first_attempts``)."""
     insts: list = [None] * count
     costs = torch.empty((count, 1 << n), dtype=torch.uint8, device="cuda")
     attempt = np.zeros(count, dtype=np.int64)
     todo = np.arange(count)
-    pool = ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1)))  # numpy's draws release the GIL
+    pool = ThreadPoolExecutor(_workers())
     while todo.size:
         if int(attempt[todo].max()) >= max_attempts:
             raise RuntimeError(f"no satisfiable CNF({n}, {k}) instance in {max_attempts} attempts")
-        cand = list(pool.map(lambda i: gen.protocol_instance(tag, n, k, start + int(i), int(attempt[i])), todo))
+        if first is not None:
+            cand, first = list(first), None
+        else:
+            cand = list(pool.map(lambda i: gen.protocol_instance(tag, n, k, start + int(i), int(attempt[i])), todo))
         cs, sols, _ = api.cost_table_batch(cand)
         ok = sols > 0
         if ok.any():
@@ -106,24 +122,47 @@ def fit_power_law(ps: Sequence[int], values: Sequence[float]):
     return float(math.exp(lna)), float(b)
 
 
+def eval_batches(ns: Iterable[int], count: int, dtype: str = "c64", mem_budget: int = 32 << 30):
+    """The evaluation's batches (n, first index, size), in order."""
+    es = 8 if dtype == "c64" else 16
+    out = []
+    for n in ns:
+        chunk = int(max(1, min(count, mem_budget // ((1 << n) * (1 + es)))))
+        out.extend((n, c0, min(chunk, count - c0)) for c0 in range(0, count, chunk))
+    return out
+
+
 def evaluate(k: int, angles: dict, ns: Iterable[int] = range(12, 20), count: int = 2500,
              tag: str = "protocol-eval", dtype: str = "c64", running_times: bool = True,
-             mem_budget: int = 32 << 30, log=None) -> dict:
+             mem_budget: int = 32 << 30, log=None, first0=None) -> dict:
     """p_hat and median running time per (p, n) for the fixed `angles`
-    ({p: (gamma, beta)}) over `count` satisfiable instances per n."""
-    es = 8 if dtype == "c64" else 16
+    ({p: (gamma, beta)}) over `count` satisfiable instances per n.  The next
+    batch's first attempts are drawn on a background thread while the GPU
+    works on the current one; `first0`, a future of the first batch's, lets
+    the caller start that earlier."""
+    ns = list(ns)
     out = {}
     stats = {"amp_layers": 0, "evolve_s": 0.0, "sample_s": 0.0, "draws": 0, "cost_s": 0.0}
+    batches = eval_batches(ns, count, dtype, mem_budget)
+    bg = ThreadPoolExecutor(1)
+    ktag = f"{tag}-k{k}"
+    n0, s0, b0 = batches[0]
+    pending = first0 if first0 is not None else bg.submit(first_attempts, ktag, n0, k, b0, s0)
+    bi = 0
     for n in ns:
-        per = (1 << n) * (1 + es)
-        chunk = int(max(1, min(count, mem_budget // per)))
         ps_all = {p: [] for p in angles}
         rts = {p: [] for p in angles}
         ms = []
-        for c0 in range(0, count, chunk):
-            B = min(chunk, count - c0)
+        while bi < len(batches) and batches[bi][0] == n:
+            _, c0, B = batches[bi]
+            first = pending.result()
+            bi += 1
+            if bi < len(batches):
+                nn, nc0, nB = batches[bi]
+                pending = bg.submit(first_attempts, ktag, nn, k, nB, nc0)
             t0 = time.perf_counter()
-            insts, costs = satisfiable_batch(f"{tag}-k{k}", n, k, B, start=c0)
+            insts, costs = satisfiable_batch(ktag, n, k, B, start=c0, first=first)
+            del first
             torch.cuda.synchronize()
             stats["cost_s"] += time.perf_counter() - t0
             ms.extend(i.m for i in insts)
@@ -156,6 +195,7 @@ def evaluate(k: int, angles: dict, ns: Iterable[int] = range(12, 20), count: int
             if log:
                 log(f"k={k} p={p} n={n}: p_hat={rec['mean_psucc']:.4g}"
                     + (f" median running time={rec['median_running_time']:.4g}" if running_times else ""))
+    bg.shutdown()
     return {"points": out, "stats": stats}
 
 
@@ -188,6 +228,10 @@ def run_protocol(ks: Sequence[int] = (9,), ps: Sequence[int] = (1, 2, 4, 8, 16, 
     result = {"ks": list(ks), "ps": list(ps), "ns": ns, "train": {"n": 12, "t": t, "epochs": epochs, "lr": lr},
               "count": count, "by_k": {}}
     for k in ks:
+        # the evaluation's first instances are drawn while the angles train
+        bg = ThreadPoolExecutor(1)
+        n0, s0, b0 = eval_batches(ns, count, dtype)[0]
+        first0 = bg.submit(first_attempts, f"protocol-eval-k{k}", n0, k, b0, s0)
         t0 = time.perf_counter()
         angles, trained = {}, {}
         for p in ps:
@@ -196,7 +240,8 @@ def run_protocol(ks: Sequence[int] = (9,), ps: Sequence[int] = (1, 2, 4, 8, 16, 
             trained[str(p)] = {"gamma": list(map(float, g)), "beta": list(map(float, b)),
                                "mean_psucc_first": trace[0][1], "mean_psucc_last": trace[-1][1]}
         t_train = time.perf_counter() - t0
-        ev = evaluate(k, angles, ns, count, dtype=dtype, running_times=running_times, log=log)
+        ev = evaluate(k, angles, ns, count, dtype=dtype, running_times=running_times, log=log, first0=first0)
+        bg.shutdown()
         ex = exponents(k, ev["points"], list(ps), ns)
         result["by_k"][str(k)] = {
             "r_hat": gen.threshold_density(k), "train_seconds": t_train, "angles": trained,
