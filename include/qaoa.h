@@ -78,7 +78,7 @@ extern "C" {
  * and the butterflies and phases run in that arithmetic on the FP32 pipes,
  * which on GB300 are far faster than the FP64 pipe.  Per-operation error about
  * 2^-45 of the operands instead of 2^-53 (n = 30, p = 10: p_succ within about
- * 1e-13 of FP64).  Small n (the one-CTA path) runs in FP64 regardless. */
+ * 1e-13 of FP64).  Small n (the one-CTA path) takes it too. */
 #define QAOA_DF64 0x4
 
 #define QAOA_MAX_N 32

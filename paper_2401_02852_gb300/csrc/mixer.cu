@@ -452,6 +452,33 @@ __device__ __forceinline__ void smem_butterfly_pass(typename Cx<R>::V *s, int n,
     }
 }
 
+// Device conversions of FP64 inputs to each arithmetic (double-float: the
+// nearest float, then the nearest float to the remainder).
+template <typename R>
+__device__ __forceinline__ R real_dev(double x) {
+    if constexpr (is_df<R>()) {
+        const float hi = __double2float_rn(x);
+        return dfloat{hi, __double2float_rn(x - (double)hi)};
+    } else {
+        return (R)x;
+    }
+}
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::V amp_dev(double re, double im) {
+    if constexpr (is_df<R>()) {
+        const dfloat r = real_dev<dfloat>(re), i = real_dev<dfloat>(im);
+        return make_float4(r.hi, r.lo, i.hi, i.lo);
+    } else {
+        typename Cx<R>::V z;
+        z.x = (R)re;
+        z.y = (R)im;
+        return z;
+    }
+}
+
+// One CTA per job: the whole evolution in shared memory.  complex128 runs in
+// FP64, or with QAOA_DF64 in double-float arithmetic (R = dfloat: float4
+// amplitudes in shared memory, FP64 (re, im) written out).
 template <typename R>
 __global__ void __launch_bounds__(PT) small_kernel(const SmallJob *jobs, const double *tables, const double *coefs,
                                                    int max_n) {
@@ -467,16 +494,11 @@ __global__ void __launch_bounds__(PT) small_kernel(const SmallJob *jobs, const d
     for (int l = 0; l < jb.p; ++l) {
         const double *tb = tables + 2 * ((size_t)jb.table_off + (size_t)l * (jb.m + 1));
         __syncthreads();
-        for (int c = threadIdx.x; c <= jb.m; c += blockDim.x) {
-            V z;
-            z.x = (R)tb[2 * c];
-            z.y = (R)tb[2 * c + 1];
-            stab[c] = z;
-        }
+        for (int c = threadIdx.x; c <= jb.m; c += blockDim.x) stab[c] = amp_dev<R>(tb[2 * c], tb[2 * c + 1]);
         __syncthreads();
         for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) s[x] = l == 0 ? stab[sc[x]] : cmul(s[x], stab[sc[x]]);
         const double *cf = coefs + 4 * ((size_t)jb.coef_off + l);
-        const R A = (R)cf[0], B = (R)cf[1];
+        const R A = real_dev<R>(cf[0]), B = real_dev<R>(cf[1]);
         const bool ua = cf[2] != 0.0;
         for (int j = 0; j < n; j += 2) {
             __syncthreads();
@@ -485,20 +507,25 @@ __global__ void __launch_bounds__(PT) small_kernel(const SmallJob *jobs, const d
     }
     if (jb.p == 0) {  // |+>: the table of "layer 0" holds the amplitude
         const double *tb = tables + 2 * (size_t)jb.table_off;
-        V z;
-        z.x = (R)tb[0];
-        z.y = (R)tb[1];
+        const V z = amp_dev<R>(tb[0], tb[1]);
         for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) s[x] = z;
     }
     __syncthreads();
     double acc[2] = {0.0, 0.0};
-    V *out = reinterpret_cast<V *>(jb.state);
     for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
         const V v = s[x];
-        const double w = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        double w;
+        if constexpr (is_df<R>()) {
+            w = amp_prob(v);
+            if (jb.state)
+                reinterpret_cast<double2 *>(jb.state)[x] =
+                    make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+        } else {
+            w = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+            if (jb.state) reinterpret_cast<V *>(jb.state)[x] = v;
+        }
         acc[1] += w;
         if (sc[x] == 0) acc[0] += w;
-        if (out) out[x] = v;
     }
     block_sum<2>(acc);
     if (threadIdx.x == 0 && jb.result) {
@@ -517,7 +544,6 @@ static size_t small_smem(int dtype, int max_n) {
 
 int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const double *d_tables, const double *d_coefs,
                        int max_n, int flags, cudaStream_t stream) {
-    (void)flags;
     const size_t smem = small_smem(dtype, max_n);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -526,12 +552,15 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
         cudaError_t e1 = cudaFuncSetAttribute(small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)small_smem(QAOA_C64, small_n_pack_limit(QAOA_C64)));
         cudaError_t e2 = cudaFuncSetAttribute(small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        attr_err = e1 != cudaSuccess ? e1 : e2;
+        cudaError_t e3 = cudaFuncSetAttribute(small_kernel<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        attr_err = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
     });
     if (attr_err != cudaSuccess) return cuda_error(attr_err, "small_kernel attributes");
     profile_before(K_SMALL_N, stream);
     if (dtype == QAOA_C64)
         small_kernel<float><<<n_jobs, PT, smem, stream>>>(d_jobs, d_tables, d_coefs, max_n);
+    else if (flags & QAOA_DF64)
+        small_kernel<dfloat><<<n_jobs, PT, smem, stream>>>(d_jobs, d_tables, d_coefs, max_n);
     else
         small_kernel<double><<<n_jobs, PT, smem, stream>>>(d_jobs, d_tables, d_coefs, max_n);
     return profile_after(K_SMALL_N, stream);

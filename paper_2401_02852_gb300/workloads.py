@@ -188,12 +188,26 @@ def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p:
     # phase multiply (4 FMA-equivalents); 2 flops per FMA.
     flops = count * (1 << n) * p * (2 * n + 4) * 2
     fp64_nominal = 1.25e12  # GB300 dense FP64, nominal (not measured here)
+    # the same batch in double-float arithmetic (QAOA_DF64)
+    from ._lib import DF64
+    stdf = torch.empty_like(states)
+    api.evolve_batch(n, costs, insts[0].m, g, b, "c128", flags=DF64, out=stdf)
+    _sync()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, psdf, _ = api.evolve_batch(n, costs, insts[0].m, g, b, "c128", flags=DF64, out=stdf)
+    _sync()
+    dtdf = (time.perf_counter() - t0) / reps
+    sol = sols > 0
     return {"count": count, "n": n, "m": insts[0].m, "p": p, "ms_per_batch": dt * 1e3,
             "amp_layer_per_s": count * (1 << n) * p / dt,
             "roofline": {"bound": "fp64", "achieved_tflops": flops / dt / 1e12, "peak_tflops": fp64_nominal / 1e12,
                          "frac": flops / dt / fp64_nominal, "peak_source": "nominal"},
             "mean_psucc": float(np.mean(ps)),
-            "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols))}
+            "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols)),
+            "df64": {"ms_per_batch": dtdf * 1e3, "speedup_over_fp64": dt / dtdf,
+                     "max_psucc_rel_diff_vs_fp64": float(np.max(np.abs(psdf[sol] - ps[sol]) / ps[sol])),
+                     "max_amp_diff_vs_fp64": float((stdf - states).abs().max())}}
 
 
 def protocol_workload(ks=(9,), ps=(1, 2, 4, 8, 16, 32), count: int = 2500, lr: float = 1e-2) -> dict:

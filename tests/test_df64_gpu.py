@@ -23,7 +23,9 @@ from paper_2401_02852_gb300 import api  # noqa: E402
 from paper_2401_02852_gb300._lib import DF64, Z2_HALF, QaoaError  # noqa: E402
 
 
-@pytest.mark.parametrize("n,p,sign", [(14, 1, 1), (17, 3, 1), (20, 6, -1), (22, 4, 1)])
+# n <= 12: the one-CTA kernel in double-float; larger n: the passes
+@pytest.mark.parametrize("n,p,sign", [(6, 2, 1), (8, 5, -1), (12, 5, 1), (14, 1, 1), (17, 3, 1), (20, 6, -1),
+                                      (22, 4, 1)])
 def test_df64_matches_oracle(n, p, sign):
     inst, _ = gen.satisfiable_instance("df64", n, 5, 8.0, n, oracle.count_solutions)
     cost_o, _, _ = oracle.cost_table(n, inst.var, inst.neg)
@@ -54,6 +56,22 @@ def test_df64_matches_fp64_and_batch():
         assert abs(nmdf[i] - 1) < 1e-10
     one, _, _ = api.evolve(n, costs[1].contiguous(), insts[1].m, g, b, "c128", flags=DF64)
     assert torch.equal(one, stdf[1])
+
+
+def test_df64_small_batch_matches_fp64():
+    """The batched one-CTA path (100 instances of n = 12, the complex128 batch
+    workload's shape) in double-float against FP64."""
+    n, p, B = 12, 5, 100
+    insts = [gen.raw_instance("df64-small", n, 3, 2.0, i) for i in range(B)]
+    costs, sols, _ = api.cost_table_batch(insts)
+    g, b = gen.linear_ramp(p)
+    st64, ps64, _ = api.evolve_batch(n, costs, insts[0].m, g, b, "c128")
+    stdf, psdf, nmdf = api.evolve_batch(n, costs, insts[0].m, g, b, "c128", flags=DF64)
+    assert float((stdf - st64).abs().max()) <= 2e-12 * (1 + n * p) * float(st64.abs().max())
+    for i in range(B):
+        if sols[i]:
+            assert abs(psdf[i] - ps64[i]) <= 1e-10 * ps64[i]
+        assert abs(nmdf[i] - 1) < 1e-10
 
 
 def test_df64_p0_is_plus_state():
