@@ -261,7 +261,9 @@ typedef struct {
     int dtype;               /* QAOA_C64 or QAOA_C128                                          */
     int small_n_max;         /* n at or below which requests are packed (0 = default)         */
     int flags;               /* mixer sign flags as for qaoa_evolve; QAOA_Z2_HALF runs the
-                                unpacked requests on the halved state (half the memory)       */
+                                unpacked requests on the halved state (half the memory);
+                                QAOA_DF64 (QAOA_C128 without QAOA_Z2_HALF) runs every request
+                                in double-float arithmetic                                    */
     int device;              /* CUDA device ordinal                                            */
     int max_n;               /* largest n accepted (0 = 30)                                    */
 } qaoa_server_opts;

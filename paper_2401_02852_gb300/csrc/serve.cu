@@ -394,8 +394,10 @@ using namespace qaoa;
 extern "C" int qaoa_server_create(const qaoa_server_opts *opts, qaoa_server **out) {
     if (!opts || !out) return set_error(QAOA_EINVAL, "NULL argument");
     if (opts->dtype != QAOA_C64 && opts->dtype != QAOA_C128) return set_error(QAOA_EINVAL, "dtype=%d", opts->dtype);
-    if (opts->flags & ~(QAOA_MIXER_RX2B | QAOA_Z2_HALF))
-        return set_error(QAOA_EINVAL, "server flags=0x%x (mixer sign and halved state only)", opts->flags);
+    if (opts->flags & ~(QAOA_MIXER_RX2B | QAOA_Z2_HALF | QAOA_DF64))
+        return set_error(QAOA_EINVAL, "server flags=0x%x (mixer sign, halved state, double-float)", opts->flags);
+    if ((opts->flags & QAOA_DF64) && (opts->dtype != QAOA_C128 || (opts->flags & QAOA_Z2_HALF)))
+        return set_error(QAOA_EINVAL, "QAOA_DF64 serves complex128 full states only");
     std::unique_ptr<qaoa_server> sv(new qaoa_server());
     sv->o = *opts;
     if (sv->o.max_batch <= 0) sv->o.max_batch = 256;

@@ -74,6 +74,22 @@ def test_df64_small_batch_matches_fp64():
         assert abs(nmdf[i] - 1) < 1e-10
 
 
+def test_df64_serving_matches_direct_evolutions():
+    """A complex128 server in double-float arithmetic (packed small requests
+    and single large ones) gives the direct QAOA_DF64 evolution's numbers."""
+    from paper_2401_02852_gb300.serve import Server
+    reqs = [(gen.raw_instance("df64-srv", n, 5, 8.0, i), n) for i, n in enumerate((10, 12, 15, 18))]
+    g, b = gen.linear_ramp(4)
+    with Server("c128", flags=DF64) as s:
+        res = [s.wait(s.submit(inst, g, b)) for inst, _ in reqs]
+    for (inst, n), r in zip(reqs, res):
+        cost = api.cost_table(inst)[0]
+        _, ps, nm = api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64)
+        _, ps64, _ = api.evolve(n, cost, inst.m, g, b, "c128")
+        assert r.status == 0 and abs(r.norm - nm) <= 1e-13
+        assert abs(r.p_succ - ps) <= 1e-13 * max(ps, 1e-300) and abs(r.p_succ - ps64) <= 1e-10 * max(ps64, 1e-300)
+
+
 def test_df64_p0_is_plus_state():
     n = 16
     inst = gen.raw_instance("df64-p0", n, 5, 8.0, 0)
@@ -97,7 +113,9 @@ def test_df64_rejects_other_modes():
         api.grad(n, cost, inst.m, g, b, "c128", flags=DF64)
     from paper_2401_02852_gb300.serve import Server
     with pytest.raises(QaoaError):
-        Server("c128", flags=DF64)
+        Server("c64", flags=DF64)
+    with pytest.raises(QaoaError):
+        Server("c128", flags=DF64 | Z2_HALF)
 
 
 @pytest.mark.slow
