@@ -96,6 +96,21 @@ def test_evolve_large_m_matches_oracle(n, k):
     assert abs(ps - ref_ps) <= 1e-4 * ref_ps and abs(norm - 1) < 1e-5
 
 
+def test_halved_state_large_m():
+    """The halved state with a long clause list gives the full state's p_succ
+    and amplitudes (global-flip symmetry, C(not x) = C(x))."""
+    from paper_2401_02852_gb300._lib import Z2_HALF
+    n = 17
+    inst, ref_cost = _sat_protocol_inst("z2m", n, 9)
+    g, b = gen.linear_ramp(5, scale=0.3)
+    cost = api.cost_table(inst)[0]
+    half = api.cost_table_half(inst)[0]
+    full, ps, _ = api.evolve(n, cost, inst.m, g, b, "c128")
+    st_h, ps_h, nm_h = api.evolve(n, half, inst.m, g, b, "c128", flags=Z2_HALF)
+    assert abs(ps_h - ps) <= 1e-12 * ps and abs(nm_h - 1) < 1e-12
+    assert float((st_h - full[: 1 << (n - 1)]).abs().max()) < 1e-13
+
+
 @pytest.mark.parametrize("n,dtype", [(12, "c128"), (15, "c128"), (15, "c64")])
 def test_grad_large_m_matches_oracle(n, dtype):
     inst, ref_cost = _sat_protocol_inst(f"grm-{n}", n, 9)

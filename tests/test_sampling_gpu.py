@@ -51,15 +51,16 @@ def test_draws_match_oracle(n, sparsity, dtype):
     assert np.all(p[got.astype(np.int64)] > 0)
 
 
-def test_halved_state_draws():
+@pytest.mark.parametrize("dtype", [np.complex128, np.complex64])
+def test_halved_state_draws(dtype):
     """Halved state (flip-symmetric psi stored for x with bit n-1 clear): a draw
     with u < 1/2 is the half's draw at 2u, one with u >= 1/2 the complement of
     the half's draw at 2u - 1."""
     n = 15
-    half = gen.random_state("gpu-z2", n - 1, 0)
+    half = gen.random_state("gpu-z2", n - 1, 0).astype(dtype).astype(np.complex128)
     full = np.concatenate([half, half[::-1]]) / np.sqrt(2)  # psi(not x) = psi(x)
     u = gen.uniforms("gpu-z2", 4000, 0)
-    got = api.sample(n, torch.from_numpy(half).cuda(), u, flags=Z2_HALF).cpu().numpy().astype(np.uint64)
+    got = api.sample(n, torch.from_numpy(half.astype(dtype)).cuda(), u, flags=Z2_HALF).cpu().numpy().astype(np.uint64)
     lo = u < 0.5
     want = np.empty_like(got)
     want[lo] = oracle.sample(n - 1, half, 2 * u[lo])
