@@ -95,3 +95,21 @@ def test_fits_recover_exact_laws():
     assert ex["by_p"][2]["relative_error"] == pytest.approx(0.25)
     assert ex["power_law_bits"][1] == pytest.approx(-1.0)
     assert ex["paper_power_law"] == protocol.PAPER_POWER_LAW[9]
+
+
+def test_evaluation_batches_and_first_attempts():
+    """The evaluation's batches cover every instance index once per n, in
+    order, within the memory budget; the prefetched first attempts are the
+    instances the rejection sampler would draw itself."""
+    ns = list(range(12, 20))
+    b = protocol.eval_batches(ns, 2500, "c64", mem_budget=2 << 30)
+    for n in ns:
+        mine = [(c0, size) for (nn, c0, size) in b if nn == n]
+        covered = [i for c0, size in mine for i in range(c0, c0 + size)]
+        assert covered == list(range(2500))
+        assert all(size * (1 << n) * 9 <= (2 << 30) or size == 1 for _, size in mine)
+    assert [nn for nn, _, _ in b] == sorted(nn for nn, _, _ in b)
+    got = protocol.first_attempts("pin-first", 13, 7, 5, start=40)
+    for i, inst in enumerate(got):
+        want = gen.protocol_instance("pin-first", 13, 7, 40 + i, 0)
+        assert np.array_equal(inst.var, want.var) and np.array_equal(inst.neg, want.neg)
