@@ -344,7 +344,8 @@ static int sample_impl(int batch, int n, const uint8_t *d_costs, const void *d_s
     if (dtype == QAOA_C64) {
         const float2 *st = reinterpret_cast<const float2 *>(d_states);
         if ((reinterpret_cast<uintptr_t>(d_states) & 15u) == 0) {
-            static const cudaError_t attr = cudaFuncSetAttribute(
+            // per call: the attribute belongs to the current device
+            const cudaError_t attr = cudaFuncSetAttribute(
                 entry_scan_kernel<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGE_BYTES);
             if (attr != cudaSuccess) return cuda_error(attr, "entry scan shared memory");
             entry_scan_kernel<float2, true><<<dim3((unsigned)ng, batch), GROUP, STAGE_BYTES, stream>>>(st, ns, d_q,
