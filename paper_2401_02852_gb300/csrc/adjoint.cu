@@ -387,10 +387,12 @@ struct AdjKernels {
 template <typename R>
 static int adj_init(AdjKernels<R> **out) {
     static std::mutex mu;
-    static int state = 0;
+    static int state[MAX_DEVICES] = {};  // per device: 0 = not yet, 1 = ok
     static AdjKernels<R> ks;
+    const int dev = current_device_slot();
+    if (dev < 0) return QAOA_ECUDA;
     std::lock_guard<std::mutex> lk(mu);
-    if (state == 0) {
+    if (!state[dev]) {
         cudaError_t e = cudaFuncSetAttribute(ks.low, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)adj_smem<R>(-1));
         if (e == cudaSuccess)
@@ -407,10 +409,9 @@ static int adj_init(AdjKernels<R> **out) {
         const int small = (int)(2 * sizeof(typename Cx<R>::V) * (size_t(1) << Cx<R>::T) + (size_t(1) << Cx<R>::T));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(small_grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
-        state = e == cudaSuccess ? 1 : -1;
         if (e != cudaSuccess) return cuda_error(e, "adjoint kernel attributes");
+        state[dev] = 1;
     }
-    if (state < 0) return set_error(QAOA_ECUDA, "adjoint kernels unavailable");
     *out = &ks;
     return QAOA_OK;
 }

@@ -545,17 +545,24 @@ static size_t small_smem(int dtype, int max_n) {
 int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const double *d_tables, const double *d_coefs,
                        int max_n, int flags, cudaStream_t stream) {
     const size_t smem = small_smem(dtype, max_n);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        const int big = (int)small_smem(QAOA_C128, small_n_pack_limit(QAOA_C128));
-        cudaError_t e1 = cudaFuncSetAttribute(small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)small_smem(QAOA_C64, small_n_pack_limit(QAOA_C64)));
-        cudaError_t e2 = cudaFuncSetAttribute(small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaError_t e3 = cudaFuncSetAttribute(small_kernel<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        attr_err = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
-    });
-    if (attr_err != cudaSuccess) return cuda_error(attr_err, "small_kernel attributes");
+    {
+        static std::mutex mu;
+        static int state[MAX_DEVICES] = {};  // per device: 0 = not yet, 1 = ok
+        const int dev = current_device_slot();
+        if (dev < 0) return QAOA_ECUDA;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!state[dev]) {
+            const int big = (int)small_smem(QAOA_C128, small_n_pack_limit(QAOA_C128));
+            cudaError_t e = cudaFuncSetAttribute(small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)small_smem(QAOA_C64, small_n_pack_limit(QAOA_C64)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(small_kernel<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+            if (e != cudaSuccess) return cuda_error(e, "small_kernel attributes");
+            state[dev] = 1;
+        }
+    }
     profile_before(K_SMALL_N, stream);
     if (dtype == QAOA_C64)
         small_kernel<float><<<n_jobs, PT, smem, stream>>>(d_jobs, d_tables, d_coefs, max_n);
@@ -674,14 +681,15 @@ template <typename R>
 static int pass_kernels(PassKernels<R> **out) {
     static std::mutex mu;
     static PassKernels<R> pk;
-    static int state = 0;  // 0 = not yet, 1 = ok, <0 = failed
+    static int state[MAX_DEVICES] = {};  // per device: 0 = not yet, 1 = ok
+    const int dev = current_device_slot();
+    if (dev < 0) return QAOA_ECUDA;
     std::lock_guard<std::mutex> lk(mu);
-    if (state == 0) {
-        cudaError_t e = pk.init();
-        state = e == cudaSuccess ? 1 : -1;
+    if (!state[dev]) {
+        const cudaError_t e = pk.init();
         if (e != cudaSuccess) return cuda_error(e, "pass kernel attributes");
+        state[dev] = 1;
     }
-    if (state < 0) return set_error(QAOA_ECUDA, "pass kernels unavailable");
     *out = &pk;
     return QAOA_OK;
 }

@@ -44,6 +44,11 @@ struct Scratch {
 // capacities (device, pinned host).  Not thread-safe per stream: one caller
 // thread per stream at a time, as for any CUDA stream.
 int scratch_for(cudaStream_t stream, size_t dev_bytes, size_t host_bytes, Scratch **out);
+// Kernel attributes (the dynamic shared-memory limit) belong to a device:
+// the current device's ordinal for per-device set-up state, or -1 with the
+// error recorded when it is out of [0, MAX_DEVICES).
+constexpr int MAX_DEVICES = 64;
+int current_device_slot();
 
 // ---------------------------------------------------------------------------
 // Instrumentation: kernel kinds, launch counting and optional event timing.

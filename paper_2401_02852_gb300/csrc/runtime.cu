@@ -56,6 +56,20 @@ int device_info(DeviceInfo *out) {
 static std::mutex g_scratch_mu;
 static std::map<std::pair<int, cudaStream_t>, Scratch> g_scratch;
 
+int current_device_slot() {
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cuda_error(e, "cudaGetDevice");
+        return -1;
+    }
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        set_error(QAOA_ERANGE, "device ordinal %d", dev);
+        return -1;
+    }
+    return dev;
+}
+
 int scratch_for(cudaStream_t stream, size_t dev_bytes, size_t host_bytes, Scratch **out) {
     int dev = 0;
     QAOA_CUDA_TRY(cudaGetDevice(&dev));
