@@ -196,9 +196,10 @@ int qaoa_success_prob_noalloc(int n, const uint8_t *d_cost, const void *d_state,
  * probabilities are integer weights on a binary scale, about 2^-44 of the
  * block's largest probability, summed exactly; the block totals are summed
  * in FP64; so it differs from a sequential FP64 scan only for u_j within
- * about 2^-40 F_total of a step of F).  An x of probability zero is never drawn; a u_j
- * <= 0 yields the first and a u_j >= 1 the last x of nonzero probability; a
- * state of norm zero draws 0.  With QAOA_Z2_HALF the state and table are the
+ * about 2^-40 F_total of a step of F; a probability below about 2^-44 of
+ * its block's largest, or below about 1e-45, weighs 0).  An x of probability
+ * zero is never drawn; a u_j <= 0 yields the first and a u_j >= 1 the last x
+ * of nonzero weight; a state of norm zero draws 0.  With QAOA_Z2_HALF the state and table are the
  * halved ones (the x with bit n-1 clear, psi(not x) = psi(x)) and draws cover
  * all 2^n assignments: u_j < 1/2 draws the stored x at 2 u_j, u_j >= 1/2 the
  * complement of the stored x drawn at 2 u_j - 1 (the same distribution; u_j
