@@ -283,7 +283,8 @@ int qaoa_serve_submit(qaoa_server *s, const naesat_instance *inst, int p, const 
                       const double *beta, uint64_t *ticket);
 /* QAOA_OK with *out filled (the ticket is then retired), QAOA_PENDING, or an error. */
 int qaoa_serve_poll(qaoa_server *s, uint64_t ticket, qaoa_result *out);
-/* Blocks until the ticket finishes or timeout_s passes (QAOA_ETIMEOUT). */
+/* Blocks until the ticket finishes or timeout_s passes (QAOA_ETIMEOUT); timeout_s
+ * must be finite and >= 0 (QAOA_EINVAL otherwise). */
 int qaoa_serve_wait(qaoa_server *s, uint64_t ticket, qaoa_result *out, double timeout_s);
 /* Cancels a request that has not started; QAOA_OK or QAOA_PENDING if running. */
 int qaoa_serve_cancel(qaoa_server *s, uint64_t ticket);

@@ -282,6 +282,11 @@ static void retire(qaoa_server *sv, Slot &s) {
 }
 
 static void fail_slot(qaoa_server *sv, Slot &s, int code) {
+    // a launch that failed part-way may still hold its job buffers
+    if (s.d_cost) cudaFreeAsync(s.d_cost, s.stream);
+    if (s.d_state) cudaFreeAsync(s.d_state, s.stream);
+    s.d_cost = s.d_state = nullptr;
+    cudaGetLastError();
     const uint64_t t = now_ns();
     for (auto &q : s.reqs) {
         qaoa_result r{};
@@ -421,8 +426,15 @@ extern "C" int qaoa_server_create(const qaoa_server_opts *opts, qaoa_server **ou
     QAOA_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
     sv->slots.resize(sv->o.n_streams);
     for (auto &s : sv->slots) {
-        QAOA_CUDA_TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
-        QAOA_CUDA_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+        cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {  // release what the earlier slots created
+            for (auto &c : sv->slots) {
+                if (c.done) cudaEventDestroy(c.done);
+                if (c.stream) cudaStreamDestroy(c.stream);
+            }
+            return cuda_error(e, "server stream or event");
+        }
     }
     qaoa_server *raw = sv.release();
     raw->worker = std::thread(scheduler, raw);
@@ -481,6 +493,8 @@ extern "C" int qaoa_serve_poll(qaoa_server *sv, uint64_t ticket, qaoa_result *ou
 
 extern "C" int qaoa_serve_wait(qaoa_server *sv, uint64_t ticket, qaoa_result *out, double timeout_s) {
     if (!sv || !out) return set_error(QAOA_EINVAL, "NULL argument");
+    if (!(timeout_s >= 0.0) || !std::isfinite(timeout_s))
+        return set_error(QAOA_EINVAL, "timeout_s=%g (a finite number of seconds >= 0)", timeout_s);
     std::unique_lock<std::mutex> lk(sv->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
     for (;;) {

@@ -78,6 +78,9 @@ def test_cancel_and_timeout():
         assert r.status in (0, -6)
         with pytest.raises(QaoaError):
             s.wait(big[-1], 1e-6)  # deadline passes before a 20-layer n=24 request finishes
+        for bad in (-1.0, float("nan"), float("inf")):
+            with pytest.raises(QaoaError):
+                s.wait(big[-1], bad)
         for b in big:
             assert s.wait(b, 300).status == 0
         with pytest.raises(QaoaError):
