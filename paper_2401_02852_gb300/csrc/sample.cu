@@ -61,7 +61,7 @@ __host__ __device__ __forceinline__ uint64_t group_count(int ns) {
 // the components are scaled by 2^(E/2) (exact), squared exactly as p + e (the
 // FMA form of Dekker's TwoProduct), p_re + p_im split by Knuth's TwoSum, and
 // W = trunc(s) + trunc(rest of the sum): FP32 and integer operations.
-// complex128: |psi|^2 2^E in FP64, truncated.
+// complex128: |psi|^2 in FP64, scaled and truncated by integer operations.
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }       // e in [-126, 127]
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
@@ -77,6 +77,20 @@ __device__ __forceinline__ long long trunc_ll(float f) {
     return (b >> 31) ? -v : v;
 }
 
+// trunc(v 2^E) for a double v from its bits with integer operations: the
+// scaling only moves the exponent, so this is exact; v <= 0 (and a subnormal
+// v, whose v 2^E is below 1 for |E| <= 200) gives 0, and results at or above
+// 2^62 (beyond any group total) saturate there.
+__device__ __forceinline__ long long scaled_trunc(double v, int E) {
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (b <= 0 || ex == 0) return 0;
+    const long long mant = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);  // v = mant 2^(ex - 1075)
+    const int sh = ex - 1075 + E;
+    if (sh >= 10) return 1LL << 62;  // mant >= 2^52
+    return sh >= 0 ? mant << sh : (sh > -53 ? mant >> -sh : 0);
+}
+
 __device__ __forceinline__ long long weight(float2 z, int E) {
     const float sc = pow2f(E / 2);
     const float re = __fmul_rn(z.x, sc), im = __fmul_rn(z.y, sc);
@@ -88,8 +102,7 @@ __device__ __forceinline__ long long weight(float2 z, int E) {
     return trunc_ll(s) + trunc_ll(t);
 }
 __device__ __forceinline__ long long weight(double2 z, int E) {
-    const double w = z.x * z.x + z.y * z.y;
-    return __double2ll_rz(w * pow2d(E));
+    return scaled_trunc(z.x * z.x + z.y * z.y, E);
 }
 // |psi(x)|^2 as a float (to choose E) and the exponent that scales a maximum m.
 __device__ __forceinline__ float prob_f(float2 z) { return z.x * z.x + z.y * z.y; }
@@ -252,10 +265,14 @@ __global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, 
     const double *Pi = P + inst * ng;
     const double total = Pi[ng - 1];
     double uj = u[inst * (uint64_t)k + j];
-    uj = uj > 0.0 ? uj : 0.0;  // u <= 0 (or NaN) draws the first x of nonzero probability
-    double t = uj * (z2 ? 2.0 * total : total);
+    // u <= 0 (or NaN) draws the first x of nonzero probability; the test on the
+    // bits keeps it off the FP64 pipe (+inf and below are the non-NaN doubles)
+    const long long ub = ord(uj);
+    uj = ub > 0 && ub <= 0x7FF0000000000000LL ? uj : 0.0;
+    double t = uj * total;
+    if (z2) t += t;  // u 2 F_half
     bool flip = false;
-    if (z2 && total > 0.0 && ord(t) >= ord(total)) {
+    if (z2 && ord(total) > 0 && ord(t) >= ord(total)) {
         flip = true;
         t -= total;
     }
@@ -271,8 +288,7 @@ __global__ void __launch_bounds__(DRAW_WARPS * 32) draw_kernel(const V *states, 
     const long long Ig = Qg[glen - 1];
     long long R = 0;
     if (!edge) {
-        const double rest = (t - (g > 0 ? Pi[g - 1] : 0.0)) * pow2d(E);  // >= 0, exact scaling
-        R = rest < 9.0e18 ? __double2ll_rz(rest) : Ig;
+        R = scaled_trunc(t - (g > 0 ? Pi[g - 1] : 0.0), E);  // P[g-1] <= t
         edge = R >= Ig;
     }
     auto ikey = [](long long v) { return v; };
