@@ -429,10 +429,8 @@ static int grad_passes(int batch, int n, const uint8_t *cost, int m, int p, cons
     const int gxf = pass_grid_x(dtype, n, batch);
     DeviceInfo di;
     if ((rc = device_info(&di))) return rc;
-    int gxa = (int)(((uint64_t)di.sms * (sizeof(R) == 4 ? 2 : 1) + batch - 1) / batch);
     const uint64_t tiles = 1ull << (n - AGeo<R>::T);
-    if (gxa < 1) gxa = 1;
-    if ((uint64_t)gxa > tiles) gxa = (int)tiles;
+    const int gxa = balanced_grid_x(di.sms * (sizeof(R) == 4 ? 2 : 1), batch, tiles);
     double *d_fpart = d_scr;                                  // batch * gxf * 2
     double *d_fres = d_fpart + (size_t)batch * gxf * 2;       // batch * 2
     double *d_apart = d_fres + (size_t)batch * 2;             // batch * p * gxa * 2

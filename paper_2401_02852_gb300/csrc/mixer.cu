@@ -694,19 +694,37 @@ static int pass_kernels(PassKernels<R> **out) {
     return QAOA_OK;
 }
 
-// Grid width per instance: enough CTAs to fill every SM, capped by the tiles.
-static int grid_x(int sms, int per_sm, int batch, uint64_t tiles) {
-    uint64_t want = (uint64_t)sms * (per_sm > 0 ? per_sm : 1);
-    want = (want + batch - 1) / batch;
-    if (want < 1) want = 1;
-    return (int)(want < tiles ? want : tiles);
+// Grid width per instance (CTAs gx x batch, CTA (x, y) takes tiles x, x + gx,
+// ... of instance y).  The CTAs run in waves of `slots` resident ones and a
+// CTA lasts about its tile count plus half a tile (its first copy overlaps
+// nothing), so gx minimises
+//   ceil(gx batch / slots) (ceil(tiles / gx) + 1/2)
+// over 1 <= gx <= min(slots, tiles), the widest on ties.  One instance gets
+// min(slots, tiles); a batch gets a width whose last wave is not left
+// part-empty for the length of a whole CTA (256 instances of 2^10 tiles on
+// 304 slots: gx = 19, 16 full waves of 54 tiles, where a width of 2 gave two
+// waves of 512 tiles, the second with 208 CTAs).
+int balanced_grid_x(int slots, int batch, uint64_t tiles) {
+    if (slots < 1) slots = 1;
+    if (batch < 1) batch = 1;
+    const uint64_t cap = tiles < (uint64_t)slots ? (tiles > 0 ? tiles : 1) : (uint64_t)slots;
+    uint64_t best = 1, best_cost = ~0ull;
+    for (uint64_t gx = 1; gx <= cap; ++gx) {
+        const uint64_t waves = (gx * (uint64_t)batch + slots - 1) / slots;
+        const uint64_t cost = waves * (2 * ((tiles + gx - 1) / gx) + 1);  // in half tiles
+        if (cost <= best_cost) {
+            best_cost = cost;
+            best = gx;
+        }
+    }
+    return (int)best;
 }
 
 int pass_grid_x(int dtype, int n, int batch) {
     DeviceInfo di;
     if (device_info(&di)) return -1;
     const int T = dtype == QAOA_C64 ? Cx<float>::T : Cx<double>::T;
-    return grid_x(di.sms, 2, batch, 1ull << (n - T));  // two persistent CTAs per SM
+    return balanced_grid_x(di.sms * 2, batch, 1ull << (n - T));  // two persistent CTAs per SM
 }
 
 // Host conversions of FP64 values to each arithmetic (double-float: the

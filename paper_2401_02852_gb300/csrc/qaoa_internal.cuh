@@ -184,6 +184,9 @@ struct EvolveReq {
 // (gx from pass_grid_x); r.d_result (if set) receives [batch][2].
 int evolve_device_impl(const EvolveReq &r, cudaStream_t stream, double *d_partials, int gx);
 int pass_grid_x(int dtype, int n, int batch);
+// Grid width per instance for `batch` instances of `tiles` tiles on `slots`
+// resident CTAs (the wave-balanced choice; 1 <= result <= min(slots, tiles)).
+int balanced_grid_x(int slots, int batch, uint64_t tiles);
 // Fixed-order sums: out[g][k] = sum_j part[g][j][k] for g < groups, k < nv <= 4.
 int launch_reduce(const double *part, int groups, int nblk, int nv, double *out, cudaStream_t stream);
 
