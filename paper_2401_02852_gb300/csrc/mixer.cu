@@ -169,19 +169,22 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
         for (int r = 0; r < NR; ++r) sp[off(r)] = v[r];
     }
     if (RED && reduce) {
-        P ps = 0, nm = 0;
+        // The thread's NR probabilities are summed pairwise in P (FP32 for
+        // complex64: relative error at most 7 u = 4.2e-7 with the two roundings
+        // of each |v|^2), then everything above the thread in FP64.
+        PairwiseSum<NR, P> ps, nm;
         const uint32_t tid = threadIdx.x;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const P w = amp_prob(v[r]);
-            nm += w;
+            nm.add(r, w);
             const uint32_t u = tile_elem<Cx<R>, LO>(tid, r);
             const bool sol = sc[Z2 ? land<Cx<R>::T>(u) : u] == 0;
-            if (sol) ps += w;
+            ps.add(r, sol ? w : P(0));
             if (sa) sa[off(r)] = sol ? v[r] : zero_amp<V>();
         }
-        acc[0] += (double)ps;
-        acc[1] += (double)nm;
+        acc[0] += (double)ps.total();
+        acc[1] += (double)nm.total();
     }
 }
 
@@ -384,24 +387,28 @@ int launch_reduce(const double *part, int groups, int nblk, int nv, double *out,
 template <typename R>
 __global__ void __launch_bounds__(PT) psucc_kernel(const typename Cx<R>::V *st, const uint8_t *cs, int n,
                                                    double *partials) {
-    constexpr int CH = 32;  // elements per thread per chunk (FP32 inner sum for c64)
+    // elements per thread per chunk, summed pairwise in R (complex64: FP32,
+    // relative error at most 7 u = 4.2e-7); chunks and threads in FP64
+    constexpr int CH = 32;
     const uint64_t N = 1ull << n;
     const uint64_t chunk = (uint64_t)PT * CH;
     double acc[2] = {0.0, 0.0};
     for (uint64_t c0 = (uint64_t)blockIdx.x * chunk; c0 < N; c0 += (uint64_t)gridDim.x * chunk) {
-        R ps = 0, nm = 0;
-#pragma unroll 8
+        PairwiseSum<CH, R> ps, nm;
+#pragma unroll
         for (int r = 0; r < CH; ++r) {
             const uint64_t g = c0 + (uint64_t)r * PT + threadIdx.x;
+            R w = 0, wsol = 0;
             if (g < N) {
                 const typename Cx<R>::V v = st[g];
-                const R w = v.x * v.x + v.y * v.y;
-                nm += w;
-                if (cs[g] == 0) ps += w;
+                w = v.x * v.x + v.y * v.y;
+                wsol = cs[g] == 0 ? w : R(0);
             }
+            nm.add(r, w);
+            ps.add(r, wsol);
         }
-        acc[0] += (double)ps;
-        acc[1] += (double)nm;
+        acc[0] += (double)ps.total();
+        acc[1] += (double)nm.total();
     }
     block_sum<2>(acc);
     if (threadIdx.x == 0) {
@@ -748,7 +755,7 @@ static float4 amp_from(float4 *, double re, double im) {
 template <typename R>
 static void fill_table(typename PassKernels<R>::Full *tab, const EvolveReq &r, int l, int sign) {
     std::vector<double> re(r.m + 1), im(r.m + 1);
-    const LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+    const LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign, arith_of(r.dtype, r.flags)) : LayerCoef{1.0, 1.0, 0.0, true};
     double scale = std::pow(k.sigma, r.n);
     if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
     phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());
@@ -767,6 +774,7 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
     if (rc) return rc;
     constexpr int T = Cx<R>::T;
     const int sign = (r.flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    const int arith = arith_of(r.dtype, r.flags);
     const bool want = r.d_result != nullptr;
     // The phase table is large: keep it off the stack.
     std::vector<char> tbuf(sizeof(typename PassKernels<R>::Full));
@@ -801,14 +809,14 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         if (a.reduce && !(L.mode == MODE_PLAIN || (L.mode == MODE_INIT && low)))
             return set_error(QAOA_ECUDA, "schedule: the last pass has mode %d", L.mode);
         a.adj = (last && r.adj) ? reinterpret_cast<V *>(r.adj) : nullptr;
-        const LayerCoef k1 = r.p > 0 ? layer_coef(r.beta[L.la], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+        const LayerCoef k1 = r.p > 0 ? layer_coef(r.beta[L.la], sign, arith) : LayerCoef{1.0, 1.0, 0.0, true};
         a.ua1 = k1.unit_a;
         a.A1 = real_from<R>(k1.A);
         a.B1 = real_from<R>(k1.B);
         a.ua2 = 1;
         a.A2 = a.B2 = real_from<R>(0.0);
         if (L.mode == MODE_FUSED) {
-            const LayerCoef k2 = layer_coef(r.beta[L.la + 1], sign);
+            const LayerCoef k2 = layer_coef(r.beta[L.la + 1], sign, arith);
             a.ua2 = k2.unit_a;
             a.A2 = real_from<R>(k2.A);
             a.B2 = real_from<R>(k2.B);
@@ -885,7 +893,7 @@ static int evolve_small(const EvolveReq &r, Scratch *sc, size_t off, cudaStream_
     SmallJob *h_jobs = reinterpret_cast<SmallJob *>(h_coef + 4 * pl);
     std::vector<double> re(r.m + 1), im(r.m + 1);
     for (int l = 0; l < pl; ++l) {
-        LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+        LayerCoef k = r.p > 0 ? layer_coef(r.beta[l], sign, arith_of(r.dtype, r.flags)) : LayerCoef{1.0, 1.0, 0.0, true};
         double scale = std::pow(k.sigma, r.n);
         if (l == 0) scale *= std::pow(2.0, -0.5 * r.n);
         phase_table(r.p > 0 ? r.gamma[l] : 0.0, scale, r.m, re.data(), im.data());

@@ -371,6 +371,26 @@ __device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_
     }
 }
 
+// Pairwise sum of NR values fed in index order (NR a power of two; the index
+// must be a compile-time constant after unrolling, so the levels stay in
+// registers): element r joins the partial sums of the completed blocks below it,
+// giving the perfectly balanced tree ((x0 + x1) + (x2 + x3)) + ... with only
+// log2(NR) + 1 values live.  For NR = 32 non-negative FP32 terms the relative
+// error is at most 5 u (u = 2^-24), against 31 u for a running sum.
+template <int NR, typename P>
+struct PairwiseSum {
+    static constexpr int LOG = NR <= 1 ? 0 : (NR <= 2 ? 1 : (NR <= 4 ? 2 : (NR <= 8 ? 3 : (NR <= 16 ? 4 : (NR <= 32 ? 5 : 6)))));
+    static_assert((1 << LOG) == NR, "NR must be a power of two up to 64");
+    P lvl[LOG + 1];
+    __device__ __forceinline__ void add(int r, P x) {
+        int k = 0;
+#pragma unroll
+        for (; k < LOG && ((r >> k) & 1); ++k) x = lvl[k] + x;
+        lvl[k] = x;
+    }
+    __device__ __forceinline__ P total() const { return lvl[LOG]; }
+};
+
 // FP64 block reduction of NV values per thread (NT threads); thread 0 gets
 // the sums.
 template <int NV, int NT = PT>

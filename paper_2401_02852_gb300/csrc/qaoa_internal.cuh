@@ -129,11 +129,18 @@ std::vector<Launch> make_adj_schedule(int n_passes, int p);
 // Host-side per-layer coefficients.  One mixer layer is
 //   prod_j [c I + i S X_j] = sigma^n prod_j [A I + i B X_j]
 // with (sigma, A, B) chosen so that A = 1 or B = 1 (one FMA per component).
+// `arith` is the arithmetic of the kernels that take A and B: the non-unit
+// coefficient is returned already rounded to it (exactly representable there)
+// and sigma is derived from that rounded value.
+enum Arith { ARITH_F32 = 0, ARITH_F64 = 1, ARITH_DF = 2 };
 struct LayerCoef {
     double sigma, A, B;
     bool unit_a;  // true: A == 1, else B == 1
 };
-LayerCoef layer_coef(double beta, int sign);
+LayerCoef layer_coef(double beta, int sign, int arith);
+inline int arith_of(int dtype, int flags) {
+    return dtype == QAOA_C64 ? ARITH_F32 : ((flags & QAOA_DF64) ? ARITH_DF : ARITH_F64);
+}
 
 // Phase table of one layer: T[c] = scale * exp(-i gamma c), c = 0..m (FP64 on
 // the host; cast to the state's element type by the caller).

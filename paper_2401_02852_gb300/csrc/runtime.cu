@@ -276,19 +276,37 @@ std::vector<Launch> make_adj_schedule(int n_passes, int p) {
     return out;
 }
 
-LayerCoef layer_coef(double beta, int sign) {
+// The non-unit coefficient as the kernels' arithmetic holds it: FP32, FP64,
+// or a double-float pair (the nearest float, then the nearest float to the
+// remainder; hi + lo is exact in FP64).
+static double coef_in_arith(double x, int arith) {
+    if (arith == ARITH_F32) return (double)(float)x;
+    if (arith == ARITH_DF) {
+        const float hi = (float)x;
+        const float lo = (float)(x - (double)hi);
+        return (double)hi + (double)lo;
+    }
+    return x;
+}
+
+LayerCoef layer_coef(double beta, int sign, int arith) {
     const double c = std::cos(beta), sn = std::sin(beta);
     const double S = sign * sn;  // butterfly: a' = c a + i S b, b' = i S a + c b
+    // sigma [x I + i y X] is unitary iff sigma^2 (x^2 + y^2) = 1.  sigma is taken
+    // from the coefficient as rounded to the kernels' arithmetic, so the product
+    // the kernels apply is unitary up to their own rounding: an FP64 sigma = cos
+    // beta beside an FP32 S / c would scale the norm by the same factor on every
+    // qubit of a layer (about 1e-6 over an n = 30, p = 10 evolution).
     LayerCoef k;
     if (std::fabs(c) >= std::fabs(S)) {
-        k.sigma = c;
         k.A = 1.0;
-        k.B = S / c;
+        k.B = coef_in_arith(S / c, arith);
+        k.sigma = std::copysign(1.0 / std::sqrt(1.0 + k.B * k.B), c);
         k.unit_a = true;
     } else {
-        k.sigma = S;
-        k.A = c / S;
+        k.A = coef_in_arith(c / S, arith);
         k.B = 1.0;
+        k.sigma = std::copysign(1.0 / std::sqrt(1.0 + k.A * k.A), S);
         k.unit_a = false;
     }
     return k;

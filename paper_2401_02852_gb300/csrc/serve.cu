@@ -142,6 +142,7 @@ static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
 static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<Req>> &batch) {
     const int B = (int)batch.size();
     const int sign = (sv->o.flags & QAOA_MIXER_RX2B) ? -1 : 1;
+    const int arith = arith_of(sv->o.dtype, sv->o.flags);
     int m_stride = 1, max_n = 1;
     size_t tab_n = 0, coef_n = 0, cost_bytes = 0;
     for (auto &q : batch) {
@@ -188,7 +189,7 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
         re.resize(mt + 1);
         im.resize(mt + 1);
         for (int l = 0; l < pl; ++l) {
-            LayerCoef k = q.p > 0 ? layer_coef(q.beta[l], sign) : LayerCoef{1.0, 1.0, 0.0, true};
+            LayerCoef k = q.p > 0 ? layer_coef(q.beta[l], sign, arith) : LayerCoef{1.0, 1.0, 0.0, true};
             double scale = std::pow(k.sigma, q.n);
             if (l == 0) scale *= std::pow(2.0, -0.5 * q.n);
             phase_table(q.p > 0 ? q.gamma[l] : 0.0, scale, mt, re.data(), im.data());
