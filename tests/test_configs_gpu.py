@@ -4,7 +4,7 @@
   one batched launch: cost tables bit-exact, p_succ within 1e-10 relative.
 * The gradient workload's shape (NAE-5-SAT, n = 22, m = 176, p = 20): the
   batched complex64 adjoint gradient of a few instances against the oracle's
-  stored-state gradient (tolerance 2e-3 of max |g|), complex128 within 1e-8.
+  stored-state gradient (tolerance 1e-6 (1 + n p) of max |g|), complex128 within 1e-8.
 """
 import numpy as np
 import pytest
@@ -47,8 +47,9 @@ def test_gradient_workload_shape_against_oracle():
     rps, rdg, rdb = oracle.grad(n, ref, g, b)
     scale = max(np.max(np.abs(rdg)), np.max(np.abs(rdb)))
     assert abs(ps[0] - rps) <= 1e-4 * rps
-    assert np.max(np.abs(dg[0] - rdg)) <= 2e-3 * scale
-    assert np.max(np.abs(db[0] - rdb)) <= 2e-3 * scale
+    tol = 1e-6 * (1 + n * p) * scale
+    assert np.max(np.abs(dg[0] - rdg)) <= tol
+    assert np.max(np.abs(db[0] - rdb)) <= tol
     p1, g1, b1 = api.grad(n, costs[0].contiguous(), insts[0].m, g, b, "c128")
     assert abs(p1 - rps) <= 1e-10 * rps
     assert np.max(np.abs(g1 - rdg)) <= 1e-8 * scale and np.max(np.abs(b1 - rdb)) <= 1e-8 * scale

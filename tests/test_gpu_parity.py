@@ -3,9 +3,14 @@
 Tolerances (written here; each follows from the rounding of the arithmetic):
   * cost table, solution count, max C: bit-exact;
   * complex128 path: p_succ relative error <= 1e-10, amplitudes within 1e-13;
-  * complex64 path: p_succ relative error <= 1e-4, norm within 1e-5, amplitudes
+  * complex64 path: p_succ relative error <= 1e-4, norm within 1e-6, amplitudes
     within 1e-6 (1 + n p) max|psi| (FP32 rounding per butterfly, n p butterflies);
-  * gradients: complex128 within 1e-8 of the oracle (relative to max |g|), complex64 within 2e-3.
+    a uniform state (gamma = 0 or no clauses) rounds every amplitude the same
+    way, so its norm drifts coherently: 1e-5 there (2 u per stage, n p stages);
+  * the reduction of a given complex64 state: within 8 u = 4.8e-7 relative
+    (pairwise FP32 sums of a thread's 32 terms, FP64 above);
+  * gradients: complex128 within 1e-8 of the oracle (relative to max |g|),
+    complex64 within 1e-6 (1 + n p) (the amplitude bound's factor).
 """
 import math
 
@@ -157,7 +162,7 @@ def test_evolve_c64_matches_oracle(n, k, m, p, sign):
     psi = oracle.evolve(n, ref_cost, g, b, -1 if sign else 1)
     ref_ps, _ = oracle.success_prob(n, ref_cost, psi)
     assert abs(ps - ref_ps) <= C64_PS_TOL * abs(ref_ps)
-    assert abs(norm - 1.0) < 1e-5
+    assert abs(norm - 1.0) < 1e-6
     got = state.cpu().numpy().astype(np.complex128)
     assert np.max(np.abs(got - psi)) <= 1e-6 * (1 + n * p) * np.max(np.abs(psi))
 
@@ -170,7 +175,7 @@ def test_p0_and_random_assignment_theorem(dtype):
     sol = int((ref_cost == 0).sum())
     cost, gsol, _ = api.cost_table(inst)
     assert gsol == sol
-    tol = 1e-12 if dtype == "c128" else 1e-5
+    tol = 1e-12 if dtype == "c128" else 1e-5  # uniform state: coherent FP32 rounding
     for g, b in [([], []), (np.zeros(3), np.array([0.3, 1.2, -0.4])), (np.array([0.5, -1.0]), np.zeros(2))]:
         _, ps, norm = api.evolve(n, cost, inst.m, g, b, dtype)
         assert abs(ps - sol / 2 ** n) <= tol * sol / 2 ** n
@@ -191,12 +196,13 @@ def test_success_prob_standalone():
     inst, ref_cost = _sat_inst("sp", n, 5, 152)
     g, b = gen.linear_ramp(4)
     cost, _, _ = api.cost_table(inst)
-    for dtype, tol in (("c128", 1e-12), ("c64", 1e-5)):
+    for dtype, tol in (("c128", 1e-12), ("c64", 8 * 2.0 ** -24)):
         state, ps, norm = api.evolve(n, cost, inst.m, g, b, dtype)
         ps2, norm2 = api.success_prob(n, cost, state)
         ref = oracle.success_prob(n, ref_cost, state.cpu().numpy().astype(np.complex128))
-        assert abs(ps2 - ref[0]) <= tol * ref[0] and abs(norm2 - ref[1]) <= tol
-        assert abs(ps2 - ps) <= tol * ps
+        assert abs(ps2 - ref[0]) <= tol * ref[0] and abs(norm2 - ref[1]) <= tol * ref[1]
+        # the fused reduction of the last pass: the same bound against the oracle
+        assert abs(ps - ref[0]) <= tol * ref[0] and abs(norm - ref[1]) <= tol * ref[1]
 
 
 @pytest.mark.parametrize("n", [12, 16])
@@ -239,7 +245,7 @@ def test_grad_matches_oracle(n, dtype, sign):
     ps, dg, db = api.grad(n, cost, inst.m, g, b, dtype, flags=sign)
     rps, rdg, rdb = oracle.grad(n, ref_cost, g, b, -1 if sign else 1)
     scale = max(np.max(np.abs(rdg)), np.max(np.abs(rdb)))
-    tol = 1e-8 if dtype == "c128" else 2e-3
+    tol = 1e-8 if dtype == "c128" else 1e-6 * (1 + n * p)
     assert abs(ps - rps) <= (1e-10 if dtype == "c128" else 1e-4) * rps
     assert np.max(np.abs(dg - rdg)) <= tol * scale
     assert np.max(np.abs(db - rdb)) <= tol * scale
@@ -281,8 +287,9 @@ def test_grad_batch_matches_single():
 @pytest.mark.slow
 def test_full_size_n30_sampled():
     n, k, r, p = 30, 5, 8.0, 10
-    inst = gen.raw_instance("full30", n, k, r, 0)
+    inst, _ = gen.satisfiable_instance("full30", n, k, r, 0, lambda x: api.cost_table(x)[1])
     cost, sol, mx = api.cost_table(inst)
+    assert sol > 0
     # sampled entries against the oracle's per-x definition
     xs = gen.rng_for("full30-xs", 0).integers(0, 1 << n, size=20000, dtype=np.uint64)
     ref = oracle.cost_samples(inst.var, inst.neg, xs)
@@ -294,15 +301,14 @@ def test_full_size_n30_sampled():
     assert torch.equal(cost[flip], cost[torch.from_numpy(xs.astype(np.int64)).cuda()])
     g, b = gen.linear_ramp(p)
     st64, ps64, nm64 = api.evolve(n, cost, inst.m, g, b, "c64")
-    assert abs(nm64 - 1) < 1e-5
+    assert abs(nm64 - 1) < 1e-6
     idx = torch.from_numpy(xs.astype(np.int64)).cuda()
     assert torch.allclose(st64[idx], st64[flip], rtol=0, atol=1e-9)
     del st64
     torch.cuda.empty_cache()
     st128, ps128, nm128 = api.evolve(n, cost, inst.m, g, b, "c128")
     assert abs(nm128 - 1) < 1e-12
-    if sol:
-        assert abs(ps64 - ps128) <= C64_PS_TOL * ps128
+    assert abs(ps64 - ps128) <= C64_PS_TOL * ps128
     del st128
     torch.cuda.empty_cache()
 
@@ -314,9 +320,10 @@ def test_max_size_n32_sampled():
     a complex64 evolution (norm, flip symmetry) and the halved state's p_succ
     against the full one."""
     n, k, r, p = 32, 5, 8.0, 2
-    inst = gen.raw_instance("full32", n, k, r, 0)
+    inst, _ = gen.satisfiable_instance("full32", n, k, r, 0, lambda x: api.cost_table(x)[1])
     assert inst.m == 256
     cost, sol, mx = api.cost_table(inst)
+    assert sol > 0
     assert mx <= 255  # a count of 256 would need every clause violated at one x
     xs = gen.rng_for("full32-xs", 0).integers(0, 1 << n, size=20000, dtype=np.uint64)
     ref = oracle.cost_samples(inst.var, inst.neg, xs)
@@ -325,7 +332,7 @@ def test_max_size_n32_sampled():
     assert int(cost.sum(dtype=torch.int64).item()) == inst.m * 2 ** (n - k + 1)
     g, b = gen.linear_ramp(p)
     st, ps, nm = api.evolve(n, cost, inst.m, g, b, "c64")
-    assert abs(nm - 1) < 1e-5
+    assert abs(nm - 1) < 1e-6
     flip = torch.from_numpy(((~xs) & np.uint64((1 << n) - 1)).astype(np.int64)).cuda()
     assert torch.allclose(st[idx], st[flip], rtol=0, atol=1e-9)
     del st
@@ -336,7 +343,6 @@ def test_max_size_n32_sampled():
     del cost
     torch.cuda.empty_cache()
     _, ps_h, nm_h = api.evolve(n, half, inst.m, g, b, "c64", flags=Z2_HALF)
-    assert abs(nm_h - 1) < 1e-5
-    if sol:
-        assert abs(ps_h - ps) <= C64_PS_TOL * ps
+    assert abs(nm_h - 1) < 1e-6
+    assert abs(ps_h - ps) <= C64_PS_TOL * ps
     torch.cuda.empty_cache()

@@ -93,7 +93,7 @@ def test_evolve_large_m_matches_oracle(n, k):
     assert abs(ps - ref_ps) <= 1e-10 * ref_ps and abs(norm - 1) < 1e-12
     assert np.max(np.abs(state.cpu().numpy() - psi)) < 1e-13
     state, ps, norm = api.evolve(n, cost, inst.m, g, b, "c64")
-    assert abs(ps - ref_ps) <= 1e-4 * ref_ps and abs(norm - 1) < 1e-5
+    assert abs(ps - ref_ps) <= 1e-4 * ref_ps and abs(norm - 1) < 1e-6
 
 
 def test_halved_state_large_m():
@@ -120,7 +120,7 @@ def test_grad_large_m_matches_oracle(n, dtype):
     ps, dg, db = api.grad(n, cost, inst.m, g, b, dtype)
     rps, rdg, rdb = oracle.grad(n, ref_cost, g, b)
     scale = max(np.max(np.abs(rdg)), np.max(np.abs(rdb)))
-    tol = 1e-8 if dtype == "c128" else 2e-3
+    tol = 1e-8 if dtype == "c128" else 1e-6 * (1 + n * p)
     assert abs(ps - rps) <= (1e-10 if dtype == "c128" else 1e-4) * rps
     assert np.max(np.abs(dg - rdg)) <= tol * scale and np.max(np.abs(db - rdb)) <= tol * scale
 

@@ -48,6 +48,31 @@ def test_noalloc_matches_success_prob_on_consecutive_calls(dtype):
             assert abs(nm - ref_nm) <= REL_TOL * abs(ref_nm)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_noalloc_grid_stride_matches_oracle(dtype):
+    """States of 2^24 and 2^26 amplitudes (each block of the fixed grid strides
+    over several chunks) against the FP64 oracle's sums of the same state:
+    complex64 within 8 u = 4.8e-7 relative (pairwise FP32 sums of a thread's
+    32 terms, FP64 above), complex128 within 1e-12."""
+    import numpy as np
+
+    import oracle
+
+    tol = 8 * 2.0 ** -24 if dtype == "c64" else 1e-12
+    for n, p in ((24, 3), (26, 2)):
+        inst = gen.raw_instance("noalloc-big", n, 5, 8.0, 0)
+        cost, _, _ = api.cost_table(inst)
+        state, _, _ = api.evolve(n, cost, inst.m, *gen.linear_ramp(p), dtype)
+        cost_o, _, _ = oracle.cost_table(n, inst.var, inst.neg)
+        ref_ps, ref_nm = oracle.success_prob(n, cost_o, state.cpu().numpy().astype(np.complex128))
+        for _ in range(2):
+            rc, ps, nm = _noalloc(n, cost, state, dtype)
+            assert rc == 0, load().qaoa_last_error()
+            assert abs(ps - ref_ps) <= tol * ref_ps + 1e-300 and abs(nm - ref_nm) <= tol * ref_nm
+        del state, cost
+        torch.cuda.empty_cache()
+
+
 def test_noalloc_rejects_out_of_range_size():
     cost = torch.zeros(16, dtype=torch.uint8, device="cuda")
     state = torch.zeros(16, dtype=torch.complex64, device="cuda")
