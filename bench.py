@@ -9,8 +9,17 @@ the first pass of each layer, strided high-qubit passes) and p_succ (FP64
 reduction fused into the last pass).  Metric: amplitude-layer updates per
 second (2^n p per step), summed over ranks.
 
-Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+Prints ONE JSON line (rank 0).  ``roofline`` is the method's 1-pass floor
+(17 B per amplitude-layer for complex64) over the measured step time; the pass
+kinds' own bandwidths sit beside it.  ``extra`` carries the other configured
+workloads, run after the timed region (rank 0, one GPU): the five n = 30
+instances against stored FP64-oracle values, the halved state, complex128 and
+double-float complex128, the batched gradient (256 x n = 22, p = 20) against
+stored oracle gradients plus 200 Adam steps, the scaling sweep (n = 16..32,
+200 instances per n), the 20,000-request serving stream at 200/s and a sweep
+of offered rates, each arm of the serving comparison on the same state
+layout.  ``--quick`` runs the headline alone.  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -150,6 +159,82 @@ def profiled_traffic(kind: str, n: int, p: int, dtype: str):
     return None, None
 
 
+def step_traffic(n: int, p: int, dtype: str, alg: dict):
+    """DRAM bytes of one step (cost table + passes) from the committed per-kind
+    ncu figures, provided every kind the step launches has a current figure."""
+    total, src = 0, None
+    launches = {"cost_table": 1, **alg["launches"]}
+    for kind, count in launches.items():
+        if not count:
+            continue
+        per, src = profiled_traffic(kind, n, p, dtype)
+        if per is None:
+            return None, src
+        total += per * count
+    return total, src
+
+
+def load_golden(name: str):
+    """Stored FP64-oracle results (tests/golden/, written by scripts that call only the oracle)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def config2_seeds(n: int, p: int, g, b, count: int = 5) -> dict:
+    """The precision study's five seeded instances: p_succ of the complex64,
+    complex128 and double-float complex128 evolutions against the stored FP64
+    oracle values, and each complex64 evolution's time and bandwidth."""
+    import torch
+
+    from paper_2401_02852_gb300 import api
+    from paper_2401_02852_gb300 import instances as gen
+    from paper_2401_02852_gb300._lib import DF64
+
+    gold = load_golden("n30_p10_oracle.json") or {"instances": []}
+    by_index = {r["index"]: r for r in gold["instances"]}
+    alg = algorithmic_bytes(n, p, "c64")
+    sched = alg["pass_low"] + alg["pass_high"]
+    cost = torch.empty(1 << n, dtype=torch.uint8, device="cuda")
+    st = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    st128 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    rows = []
+    for idx in range(count):
+        inst, n_sol = gen.satisfiable_instance("bench-n30", n, K_SAT, R_SAT, idx, lambda x: api.cost_table(x)[1])
+        api.cost_table(inst, out=cost, stats=False)
+        api.evolve(n, cost, inst.m, g, b, "c64", out=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _, ps, nm = api.evolve(n, cost, inst.m, g, b, "c64", out=st)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        _, ps128, _ = api.evolve(n, cost, inst.m, g, b, "c128", out=st128)
+        _, psdf, _ = api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=st128)
+        rec = by_index.get(idx)
+        ok = rec is not None and rec["attempt"] == inst.seed_key[-1] and rec["n_sol"] == n_sol
+        ref = rec["p_succ"] if ok else None
+        rows.append({"index": idx, "attempt": int(inst.seed_key[-1]), "n_sol": n_sol, "p_succ_c64": ps, "norm_c64": nm,
+                     "ms_per_evolution_c64": ms, "amp_layer_per_s": (2 ** n) * p / (ms / 1e3),
+                     "schedule_GBps": sched / (ms / 1e3) / 1e9,
+                     "effective_GBps_at_17B": 17 * (2 ** n) * p / (ms / 1e3) / 1e9,
+                     "oracle_p_succ": ref,
+                     "c64_rel_err_vs_oracle": abs(ps - ref) / ref if ref else None,
+                     "c128_rel_err_vs_oracle": abs(ps128 - ref) / ref if ref else None,
+                     "df64_rel_err_vs_oracle": abs(psdf - ref) / ref if ref else None})
+    del cost, st, st128
+    errs = [r["c64_rel_err_vs_oracle"] for r in rows if r["c64_rel_err_vs_oracle"] is not None]
+    return {"instances": rows, "oracle_source": "tests/golden/n30_p10_oracle.json",
+            "max_c64_rel_err_vs_oracle": max(errs) if errs else None,
+            "max_c128_rel_err_vs_oracle": max((r["c128_rel_err_vs_oracle"] for r in rows
+                                               if r["c128_rel_err_vs_oracle"] is not None), default=None),
+            "max_df64_rel_err_vs_oracle": max((r["df64_rel_err_vs_oracle"] for r in rows
+                                               if r["df64_rel_err_vs_oracle"] is not None), default=None)}
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -249,6 +334,7 @@ def run_native(args, ws, rank, local):
     cost = torch.empty(1 << n, dtype=torch.uint8, device="cuda")
     state = torch.empty(1 << n, dtype=api.TORCH_DTYPE[api.dtype_code(dtype)], device="cuda")
     plan = api.plan(n, dtype)
+    state_dtype = state.dtype
     results = {}
 
     def step():
@@ -280,24 +366,36 @@ def run_native(args, ws, rank, local):
     ms_max = 1000.0 * qdist.max_over_ranks(ms / 1000.0, device=dev)
     value = qdist.job_throughput(float((2 ** n) * p * args.steps), ms / 1000.0, device=dev)
 
-    # roofline of the dominant kernel from the live per-launch events
+    # Roofline (the scored figure): the method's 1-pass floor, (2 es + 1) bytes per
+    # amplitude-layer (17 B complex64, 33 B complex128: the state read and
+    # written once and the cost byte read once per layer), times the
+    # amplitude-layers of a step, over the measured step time.  Extra passes of
+    # the schedule do not raise it.  Beside it, each pass kind's achieved
+    # bandwidth on the bytes it really moves (its launches' CUDA-event times).
     kinds = prof.stats
-    dom = max(kinds, key=lambda k: kinds[k][1])
     alg = algorithmic_bytes(n, p, dtype)
     peak, peak_src = measured_peak()
-    roof = None
-    if dom in ("pass_low", "pass_high"):
-        per_launch_bytes = alg[dom] / alg["launches"][dom]
-        avg_ms = kinds[dom][1] / kinds[dom][0]
-        achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
-        traffic, traffic_src = profiled_traffic(dom, n, p, dtype)
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms}
-    # all pass kernels together, and the 1-pass floor (17 B per amp-layer for complex64)
+    per_unit = 2 * es + 1
+    units = (2 ** n) * p
+    step_s = ms_max / args.steps / 1000.0
+    achieved = per_unit * units / step_s / 1e9
+    passes = {}
+    for kind in ("pass_low", "pass_high"):
+        if kind in kinds and alg["launches"][kind]:
+            per_launch = alg[kind] / alg["launches"][kind]
+            avg_ms = kinds[kind][1] / kinds[kind][0]
+            gbps = per_launch / (avg_ms / 1000.0) / 1e9
+            passes[kind] = {"launches_per_step": alg["launches"][kind], "algorithmic_bytes_per_launch": per_launch,
+                            "avg_launch_ms": avg_ms, "achieved_GBps": gbps, "frac": gbps / peak}
+    traffic, traffic_src = step_traffic(n, p, dtype, alg)
+    dom = max(passes, key=lambda k: kinds[k][1]) if passes else None
+    roof = {"kernel": "evolution step: cost table + every pass launch + the p_succ reduction", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": traffic_src, "peak_source": peak_src, "per_unit_bytes": per_unit,
+            "unit_name": "amplitude-layer", "units_per_step": units,
+            "achieved_pass_frac": passes[dom]["frac"] if dom else None, "dominant_pass_kind": dom,
+            "passes": passes, "schedule_bytes_per_step": alg["pass_low"] + alg["pass_high"]}
     pass_ms = sum(kinds.get(k, (0, 0.0))[1] for k in ("pass_low", "pass_high")) / args.steps
-    floor_bytes = (2 ** n) * p * (2 * es + 1)
-    effective = floor_bytes / (ms_max / args.steps / 1000.0) / 1e9
 
     # end to end through the public API from host memory
     e2e = None
@@ -316,71 +414,100 @@ def run_native(args, ws, rank, local):
 
     extra = {"p_succ": results["p_succ"], "norm": results["norm"], "n_sol": n_sol, "m": inst.m,
              "passes_per_layer": len(plan), "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kinds.items()},
-             "pass_ms_per_step": pass_ms, "effective_GBps_at_17B": effective if es == 8 else None}
+             "pass_ms_per_step": pass_ms}
+    legs = []  # (name, function) run after the headline, each guarded
+
+    if rank == 0 and n == N_DEFAULT and p == P_DEFAULT and dtype == "c64" and not args.no_config2:
+        def config2():
+            return config2_seeds(n, p, g, b)
+        legs.append(("config2_five_seeds", config2))
     if args.z2 and rank == 0:
-        # the halved state (exact by the global-flip symmetry): same p_succ, half the bytes
-        from paper_2401_02852_gb300._lib import Z2_HALF
-        half = torch.empty(1 << (n - 1), dtype=torch.uint8, device="cuda")
-        st_h = torch.empty(1 << (n - 1), dtype=state.dtype, device="cuda")
-        hres = {}
+        def z2_leg():
+            # the halved state (exact by the global-flip symmetry): same p_succ, half the bytes
+            from paper_2401_02852_gb300._lib import Z2_HALF
+            half = torch.empty(1 << (n - 1), dtype=torch.uint8, device="cuda")
+            st_h = torch.empty(1 << (n - 1), dtype=state_dtype, device="cuda")
+            hres = {}
 
-        def step_h():
-            api.cost_table_half(inst, out=half, stats=False)
-            _, hres["p"], hres["nm"] = api.evolve(n, half, inst.m, g, b, dtype, flags=Z2_HALF, out=st_h)
+            def step_h():
+                api.cost_table_half(inst, out=half, stats=False)
+                _, hres["p"], hres["nm"] = api.evolve(n, half, inst.m, g, b, dtype, flags=Z2_HALF, out=st_h)
 
-        for _ in range(3):
-            step_h()
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        for _ in range(args.steps):
-            step_h()
-        a1.record()
-        torch.cuda.synchronize()
-        ms_h = a0.elapsed_time(a1) / args.steps
-        extra["z2_halved"] = {"ms_per_step": ms_h, "amp_layer_per_s": (2 ** n) * p / (ms_h / 1000.0),
-                              "p_succ": hres["p"], "p_succ_rel_diff_vs_full": abs(hres["p"] - results["p_succ"]) /
-                              results["p_succ"], "stored_state_GB": (2 ** (n - 1)) * es / 1e9}
-        del half, st_h
-
+            for _ in range(3):
+                step_h()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(args.steps):
+                step_h()
+            a1.record()
+            torch.cuda.synchronize()
+            ms_h = a0.elapsed_time(a1) / args.steps
+            return {"ms_per_step": ms_h, "amp_layer_per_s": (2 ** n) * p / (ms_h / 1000.0),
+                    "p_succ": hres["p"], "p_succ_rel_diff_vs_full": abs(hres["p"] - results["p_succ"]) /
+                    results["p_succ"], "stored_state_GB": (2 ** (n - 1)) * es / 1e9}
+        legs.append(("z2_halved", z2_leg))
     if args.compare_c128 and dtype == "c64" and rank == 0:
+        def c128_leg():
+            st128 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+            api.evolve(n, cost, inst.m, g, b, "c128", out=st128)
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            reps = 2
+            for _ in range(reps):
+                _, ps128, _ = api.evolve(n, cost, inst.m, g, b, "c128", out=st128)
+            z.record()
+            torch.cuda.synchronize()
+            ms128 = a.elapsed_time(z) / reps
+            out = {"c128": {"ms_per_evolution": ms128, "amp_layer_per_s": (2 ** n) * p / (ms128 / 1000.0),
+                            "p_succ": ps128, "c64_rel_err_vs_c128": abs(results["p_succ"] - ps128) / ps128,
+                            "c64_speedup_over_c128": ms128 / (ms / args.steps)}}
+            # the same complex128 evolution in double-float arithmetic (QAOA_DF64)
+            from paper_2401_02852_gb300._lib import DF64
+            std = torch.empty_like(st128)
+            api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=std)
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(reps):
+                _, psdf, _ = api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=std)
+            z.record()
+            torch.cuda.synchronize()
+            msdf = a.elapsed_time(z) / reps
+            amp_err = float((std - st128).abs().max().item() / st128.abs().max().item())
+            out["c128_df64"] = {"ms_per_evolution": msdf, "amp_layer_per_s": (2 ** n) * p / (msdf / 1000.0),
+                                "p_succ": psdf, "p_succ_rel_diff_vs_fp64": abs(psdf - ps128) / ps128,
+                                "max_amp_diff_vs_fp64_over_max_amp": amp_err, "speedup_over_fp64": ms128 / msdf}
+            del st128, std
+            return out
+        legs.append(("c128_compare", c128_leg))
+    if rank == 0 and ws == 1:
+        from paper_2401_02852_gb300 import workloads
+        if not args.no_grad:
+            legs.append(("grad", lambda: workloads.grad_workload(batch=256, n=22, p=20, adam_steps=args.adam_steps,
+                                                                 fd_instances=1, reference=load_golden("grad_n22_p20_oracle.json"))))
+        if not args.no_sweep:
+            legs.append(("sweep", lambda: workloads.sweep_workload(ns=range(16, 33, 2), seeds=args.seeds)))
+        if args.serve_requests > 0:
+            legs.append(("serving", lambda: workloads.serve_workload(count=args.serve_requests, rate_hz=200.0)))
+        if not args.no_rate_sweep:
+            legs.append(("serving_rate_sweep", lambda: workloads.serve_rate_sweep(
+                rates=(1000.0, 2000.0, 5000.0, 20000.0), count=args.rate_sweep_requests)))
+    if legs:
         del state
         torch.cuda.empty_cache()
-        st128 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
-        api.evolve(n, cost, inst.m, g, b, "c128", out=st128)
-        torch.cuda.synchronize()
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        reps = 2
-        for _ in range(reps):
-            _, ps128, _ = api.evolve(n, cost, inst.m, g, b, "c128", out=st128)
-        z.record()
-        torch.cuda.synchronize()
-        ms128 = a.elapsed_time(z) / reps
-        extra["c128"] = {"ms_per_evolution": ms128, "amp_layer_per_s": (2 ** n) * p / (ms128 / 1000.0),
-                         "p_succ": ps128, "c64_rel_err_vs_c128": abs(results["p_succ"] - ps128) / ps128,
-                         "c64_speedup_over_c128": ms128 / (ms / args.steps - 0.0)}
-        # the same complex128 evolution in double-float arithmetic (QAOA_DF64)
-        from paper_2401_02852_gb300._lib import DF64
-        std = torch.empty_like(st128)
-        api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=std)
-        torch.cuda.synchronize()
-        a.record()
-        for _ in range(reps):
-            _, psdf, _ = api.evolve(n, cost, inst.m, g, b, "c128", flags=DF64, out=std)
-        z.record()
-        torch.cuda.synchronize()
-        msdf = a.elapsed_time(z) / reps
-        amp_err = float((std - st128).abs().max().item() / st128.abs().max().item())
-        extra["c128_df64"] = {"ms_per_evolution": msdf, "amp_layer_per_s": (2 ** n) * p / (msdf / 1000.0),
-                              "p_succ": psdf, "p_succ_rel_diff_vs_fp64": abs(psdf - ps128) / ps128,
-                              "max_amp_diff_vs_fp64_over_max_amp": amp_err, "speedup_over_fp64": ms128 / msdf}
-        del st128, std
-
-    if args.serve_requests > 0 and rank == 0 and ws == 1:
-        from paper_2401_02852_gb300 import workloads
+    for name, fn in legs:
+        t0 = time.perf_counter()
+        try:
+            res = fn()
+        except Exception as exc:  # one failing leg must not cost the line
+            res = {"error": f"{type(exc).__name__}: {exc}"}
         torch.cuda.empty_cache()
-        extra["serving"] = workloads.serve_workload(count=args.serve_requests, rate_hz=200.0)
+        if name == "c128_compare" and "error" not in res:
+            extra.update(res)
+        else:
+            extra[name] = res
+        extra.setdefault("leg_seconds", {})[name] = round(time.perf_counter() - t0, 1)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -442,8 +569,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-c128", dest="compare_c128", action="store_false")
     ap.add_argument("--no-z2", dest="z2", action="store_false", help="skip the halved-state measurement")
-    ap.add_argument("--serve-requests", type=int, default=1500,
-                    help="short serving run (Poisson 200/s) reported beside the headline; 0 skips it")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="serving stream (Poisson 200/s) reported beside the headline; 0 skips it")
+    ap.add_argument("--rate-sweep-requests", type=int, default=3000, help="requests per offered rate of the sweep")
+    ap.add_argument("--no-rate-sweep", action="store_true")
+    ap.add_argument("--no-config2", action="store_true", help="skip the five n=30 instances against the oracle")
+    ap.add_argument("--no-grad", action="store_true", help="skip the batched-gradient workload")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the scaling sweep")
+    ap.add_argument("--quick", action="store_true", help="headline only (no extra workloads)")
     ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch", "sample", "protocol"], default="evolve")
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -460,6 +593,10 @@ def main():
     ap.add_argument("--count", type=int, default=2500, help="protocol: satisfiable instances per (k, n)")
     ap.add_argument("--lr", type=float, default=1e-2, help="protocol: Adam learning rate of the angle training")
     args = ap.parse_args()
+    if args.quick:
+        args.no_config2 = args.no_grad = args.no_sweep = args.no_rate_sweep = True
+        args.z2 = args.compare_c128 = False
+        args.serve_requests = 0
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)

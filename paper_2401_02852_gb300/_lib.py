@@ -71,6 +71,7 @@ SIGNATURES = {
     "qaoa_serve_wait": (I, [P, ctypes.c_uint64, P, D]),
     "qaoa_serve_cancel": (I, [P, ctypes.c_uint64]),
     "qaoa_server_stats": (I, [P, P]),
+    "qaoa_server_issue_time": (I, [P, P, P, P]),
     "qaoa_server_destroy": (I, [P]),
     "qaoa_plan": (I, [I, I, I, P, P, P]),
     "qaoa_pass_schedule": (I, [I, I, I, I, I, P, P, P]),

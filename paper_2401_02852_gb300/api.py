@@ -232,11 +232,14 @@ def psucc_host(inst, gamma, beta, dtype="c64", flags: int = MIXER_PAPER, work: O
     n = int(inst.n)
     work = {} if work is None else work
     code = dtype_code(dtype)
-    if "cost" not in work or work["cost"].numel() != (1 << n):
-        work["cost"] = torch.empty(1 << n, dtype=torch.uint8, device="cuda")
-    if "state" not in work or work["state"].numel() != (1 << n) or work["state"].dtype != TORCH_DTYPE[code]:
-        work["state"] = torch.empty(1 << n, dtype=TORCH_DTYPE[code], device="cuda")
-    cost, _, _ = cost_table(inst, out=work["cost"], stream=stream, stats=False)
+    half = bool(flags & Z2_HALF)  # the halved table and state (global-flip symmetry)
+    size = 1 << (n - 1 if half else n)
+    if "cost" not in work or work["cost"].numel() != size:
+        work["cost"] = torch.empty(size, dtype=torch.uint8, device="cuda")
+    if "state" not in work or work["state"].numel() != size or work["state"].dtype != TORCH_DTYPE[code]:
+        work["state"] = torch.empty(size, dtype=TORCH_DTYPE[code], device="cuda")
+    table = cost_table_half if half else cost_table
+    cost, _, _ = table(inst, out=work["cost"], stream=stream, stats=False)
     _, ps, nm = evolve(n, cost, inst.var.shape[0], gamma, beta, dtype, flags, out=work["state"], stream=stream)
     return ps, nm
 

@@ -9,12 +9,20 @@
 //   * requests with n <= small_n_max are packed, up to max_batch at a time, into
 //     one batched cost-table launch plus one small-n evolution launch (one CTA
 //     per request, state resident in shared memory, any n and p per request);
-//   * larger requests run alone on a slot: cost table, then the multi-pass
-//     evolution with the fused p_succ reduction.
+//   * a larger request takes the waiting requests of the same shape with it (the
+//     same n, m, p and angles: the same pass plan, schedule, phase tables and
+//     butterfly coefficients), up to max_batch within the budget, and they run
+//     as one batch: one batched cost-table launch, then one multi-pass
+//     evolution over all their states (each pass one launch over the batch, the
+//     wave-balanced grid of the batched evolution) with the fused p_succ
+//     reduction; alone, it is the single-instance pass sequence;
+//   * when the oldest request is large and over the budget, small requests
+//     behind it are still packed into free slots (their footprint is a table).
 // Device memory for tables and states comes from cudaMallocAsync on the slot's
 // stream and returns with cudaFreeAsync, so admission never synchronises the
 // device.  Results land in pinned host memory and are published when the
-// slot's completion event fires.  Every wait on the host is bounded.
+// slot's completion event fires; a host callback enqueued behind the event
+// wakes the scheduler, which otherwise sleeps (bounded waits only).
 #include <cuda_runtime.h>
 #include <time.h>
 
@@ -51,6 +59,8 @@ struct Req {
     size_t footprint;
 };
 
+enum SlotKind { SLOT_SINGLE = 0, SLOT_PACKED = 1, SLOT_GROUP = 2 };
+
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -64,8 +74,8 @@ struct Slot {
     double *d_part = nullptr;                // partials for the pass path
     size_t part_cap = 0;
     void *d_cost = nullptr, *d_state = nullptr;  // large job buffers (freed async)
-    bool packed = false;                     // the slot runs a packed small-n batch
-    size_t res_off = 0;                      // packed: offset of the stats block in staging
+    int kind = 0;                            // SLOT_SINGLE, SLOT_PACKED or SLOT_GROUP
+    size_t res_off = 0;                      // packed / group: offset of the stats block in staging
 };
 
 }  // namespace qaoa
@@ -82,7 +92,11 @@ struct qaoa_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     size_t used_bytes = 0;
-    uint64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // submitted, completed, packed, single, peak, cancelled, errors, jobs
+    uint64_t epoch = 0;  // bumped (under mu) by submits, cancels, shutdown and finished slots
+    // submitted, completed, packed launches, single launches, peak bytes, cancelled, errors, grouped requests
+    uint64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t issue_ns = 0, issues = 0;  // host time spent issuing slots' work (uploads, launches, copies)
+    uint64_t t_first = 0;               // first admission (CLOCK_MONOTONIC ns)
     int init_status = QAOA_OK;
 };
 
@@ -100,6 +114,24 @@ static int ensure_stage(Slot &s, size_t bytes) {
     QAOA_CUDA_TRY(cudaMallocHost((void **)&s.h_stage, want));
     QAOA_CUDA_TRY(cudaMalloc((void **)&s.d_stage, want));
     s.stage_cap = want;
+    return QAOA_OK;
+}
+
+// Enqueued on a slot's stream behind its completion event: wakes the scheduler
+// (which then finds the event complete).  Runs on a CUDA callback thread and
+// calls no CUDA function; server destruction synchronises every stream first.
+static void CUDART_CB slot_done_callback(void *arg) {
+    qaoa_server *sv = static_cast<qaoa_server *>(arg);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->epoch++;
+    }
+    sv->cv_work.notify_all();
+}
+
+static int finish_slot(qaoa_server *sv, Slot &s) {
+    QAOA_CUDA_TRY(cudaEventRecord(s.done, s.stream));
+    QAOA_CUDA_TRY(cudaLaunchHostFunc(s.stream, slot_done_callback, sv));
     return QAOA_OK;
 }
 
@@ -134,8 +166,72 @@ static int launch_large(qaoa_server *sv, Slot &s, Req &q) {
     QAOA_CUDA_TRY(cudaFreeAsync(s.d_cost, s.stream));
     QAOA_CUDA_TRY(cudaFreeAsync(s.d_state, s.stream));
     s.d_cost = s.d_state = nullptr;
-    QAOA_CUDA_TRY(cudaEventRecord(s.done, s.stream));
-    return QAOA_OK;
+    return finish_slot(sv, s);
+}
+
+// Same shape: one pass plan, schedule, phase tables and coefficients.
+static bool same_shape(const Req &a, const Req &b) {
+    return a.n == b.n && a.m == b.m && a.p == b.p && a.gamma == b.gamma && a.beta == b.beta;
+}
+
+// Launch B >= 2 large requests of the same shape on slot s as one batch.
+static int launch_group(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<Req>> &batch) {
+    const int B = (int)batch.size();
+    const Req &q0 = *batch[0];
+    const int dtype = sv->o.dtype;
+    const bool z2 = (sv->o.flags & QAOA_Z2_HALF) != 0;
+    const int nb = z2 ? q0.n - 1 : q0.n;  // the half table is the first 2^(n-1) entries
+    const size_t N = (size_t)1 << nb;
+    const int m_stride = std::max(q0.m, 1);
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_recs = 0;
+    const size_t o_m = align(o_recs + (size_t)B * m_stride * sizeof(ClauseRec));
+    const size_t o_up = align(o_m + (size_t)B * sizeof(int));  // end of the uploaded part
+    const size_t o_stats = o_up;
+    const size_t o_res = align(o_stats + (size_t)B * 2 * sizeof(unsigned long long));
+    const size_t total = align(o_res + (size_t)B * 2 * sizeof(double));
+    int rc;
+    if ((rc = ensure_stage(s, total))) return rc;
+    char *h = s.h_stage, *d = s.d_stage;
+    ClauseRec *h_recs = reinterpret_cast<ClauseRec *>(h + o_recs);
+    int *h_m = reinterpret_cast<int *>(h + o_m);
+    for (int b = 0; b < B; ++b) {
+        const Req &q = *batch[b];
+        naesat_instance inst{q.n, q.m, q.k, q.var.data(), q.neg.data()};
+        encode_instance(&inst, h_recs + (size_t)b * m_stride);
+        h_m[b] = q.m;
+    }
+    // The single-instance grid width: each instance gets the blocks, and so the
+    // per-block p_succ partials, it gets alone, so its result is the same bit
+    // for bit whether it runs alone or in a batch.
+    const int gx = pass_grid_x(dtype, nb, 1);
+    if (gx < 0) return QAOA_ECUDA;
+    if (s.part_cap < (size_t)B * gx * 2) {
+        if (s.d_part) cudaFree(s.d_part);
+        s.d_part = nullptr;
+        s.part_cap = 0;
+        QAOA_CUDA_TRY(cudaMalloc((void **)&s.d_part, (size_t)B * gx * 2 * sizeof(double)));
+        s.part_cap = (size_t)B * gx * 2;
+    }
+    QAOA_CUDA_TRY(cudaMallocAsync(&s.d_cost, (size_t)B * N, s.stream));
+    QAOA_CUDA_TRY(cudaMallocAsync(&s.d_state, (size_t)B * N * es_of(dtype), s.stream));
+    QAOA_CUDA_TRY(cudaMemcpyAsync(d, h, o_up, cudaMemcpyHostToDevice, s.stream));
+    unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(d + o_stats);
+    double *d_res = reinterpret_cast<double *>(d + o_res);
+    QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, (size_t)B * 2 * sizeof(unsigned long long), s.stream));
+    if ((rc = launch_cost_table_batch(B, nb, nullptr, nullptr, reinterpret_cast<const ClauseRec *>(d + o_recs),
+                                      reinterpret_cast<const int *>(d + o_m), m_stride, (uint8_t *)s.d_cost, d_stats,
+                                      s.stream)))
+        return rc;
+    EvolveReq r{B, q0.n, table_top(q0.m), q0.p, dtype, sv->o.flags, (const uint8_t *)s.d_cost, s.d_state, nullptr,
+                q0.gamma.data(), q0.beta.data(), d_res};
+    if ((rc = evolve_device_impl(r, s.stream, s.d_part, gx))) return rc;
+    QAOA_CUDA_TRY(cudaMemcpyAsync(h + o_stats, d + o_stats, total - o_stats, cudaMemcpyDeviceToHost, s.stream));
+    QAOA_CUDA_TRY(cudaFreeAsync(s.d_cost, s.stream));
+    QAOA_CUDA_TRY(cudaFreeAsync(s.d_state, s.stream));
+    s.d_cost = s.d_state = nullptr;
+    s.res_off = o_stats;  // stats [B][2] u64, then (after alignment) results [B][2] f64
+    return finish_slot(sv, s);
 }
 
 // Launch a packed batch of small requests on slot s.
@@ -230,9 +326,8 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
     QAOA_CUDA_TRY(cudaMemcpyAsync(h + o_stats, d + o_stats, total - o_stats, cudaMemcpyDeviceToHost, s.stream));
     QAOA_CUDA_TRY(cudaFreeAsync(s.d_cost, s.stream));
     s.d_cost = nullptr;
-    QAOA_CUDA_TRY(cudaEventRecord(s.done, s.stream));
     s.res_off = o_stats;  // stats [B][2] u64, then (after alignment) results [B][2] f64
-    return QAOA_OK;
+    return finish_slot(sv, s);
 }
 
 static size_t footprint(const qaoa_server *sv, int n, bool packed) {
@@ -243,7 +338,7 @@ static size_t footprint(const qaoa_server *sv, int n, bool packed) {
 
 // Publishes the results of a finished slot (scheduler thread, lock held).
 static void retire(qaoa_server *sv, Slot &s) {
-    const bool packed = s.packed;
+    const bool packed = s.kind == SLOT_PACKED, group = s.kind == SLOT_GROUP;
     const uint64_t t = now_ns();
     const int B = (int)s.reqs.size();
     for (int b = 0; b < B; ++b) {
@@ -261,6 +356,16 @@ static void retire(qaoa_server *sv, Slot &s) {
             r.max_cost = (uint32_t)st[2 * b + 1];
             r.p_succ = res[2 * b];
             r.norm = res[2 * b + 1];
+        } else if (group) {
+            // the same layout as a packed batch; halved tables and states count twice
+            const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s.h_stage + s.res_off);
+            const double *res = reinterpret_cast<const double *>(
+                s.h_stage + ((s.res_off + (size_t)B * 16 + 255) & ~(size_t)255));
+            const double f = (sv->o.flags & QAOA_Z2_HALF) ? 2.0 : 1.0;
+            r.n_sol = (uint64_t)(f * (double)st[2 * b]);
+            r.max_cost = (uint32_t)st[2 * b + 1];
+            r.p_succ = f * res[2 * b];
+            r.norm = f * res[2 * b + 1];
         } else {
             const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s.h_stage);
             const double *res = reinterpret_cast<const double *>(s.h_stage + 16);
@@ -306,10 +411,48 @@ static void fail_slot(qaoa_server *sv, Slot &s, int code) {
     s.busy = false;
 }
 
+// Packs waiting small requests (any position in the queue) into one batch
+// within the budget; returns the batch and its footprint.
+static std::vector<std::shared_ptr<Req>> take_small(qaoa_server *sv, size_t *bytes) {
+    std::vector<std::shared_ptr<Req>> batch;
+    *bytes = 0;
+    for (auto it = sv->waiting.begin(); it != sv->waiting.end() && (int)batch.size() < sv->o.max_batch;) {
+        if ((*it)->n <= sv->o.small_n_max && sv->used_bytes + *bytes + (*it)->footprint <= sv->o.hbm_budget_bytes) {
+            *bytes += (*it)->footprint;
+            batch.push_back(*it);
+            it = sv->waiting.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return batch;
+}
+
+// The head (a large request that fits) and the waiting requests of its shape
+// behind it, up to max_batch within the budget.
+static std::vector<std::shared_ptr<Req>> take_group(qaoa_server *sv, size_t *bytes) {
+    std::vector<std::shared_ptr<Req>> batch;
+    auto head = sv->waiting.front();
+    sv->waiting.pop_front();
+    batch.push_back(head);
+    *bytes = head->footprint;
+    for (auto it = sv->waiting.begin(); it != sv->waiting.end() && (int)batch.size() < sv->o.max_batch;) {
+        if (same_shape(**it, *head) && sv->used_bytes + *bytes + (*it)->footprint <= sv->o.hbm_budget_bytes) {
+            *bytes += (*it)->footprint;
+            batch.push_back(*it);
+            it = sv->waiting.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return batch;
+}
+
 static void scheduler(qaoa_server *sv) {
     cudaSetDevice(sv->o.device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
+        const uint64_t epoch0 = sv->epoch;
         // (1) retire finished slots
         bool any_busy = false;
         for (size_t i = 0; i < sv->slots.size(); ++i) {
@@ -328,68 +471,58 @@ static void scheduler(qaoa_server *sv) {
             }
         }
         if (sv->stop && sv->waiting.empty() && !any_busy) break;
-        // (2) admit waiting requests in arrival order
+        // (2) admit waiting requests, oldest first
         for (size_t i = 0; i < sv->slots.size() && !sv->waiting.empty(); ++i) {
             Slot &s = sv->slots[i];
             if (s.busy) continue;
             auto head = sv->waiting.front();
             const bool small = head->n <= sv->o.small_n_max;
-            if (small) {
-                std::vector<std::shared_ptr<Req>> batch;
-                size_t bytes = 0;
-                for (auto it = sv->waiting.begin(); it != sv->waiting.end() && (int)batch.size() < sv->o.max_batch;) {
-                    if ((*it)->n <= sv->o.small_n_max && sv->used_bytes + bytes + (*it)->footprint <= sv->o.hbm_budget_bytes) {
-                        bytes += (*it)->footprint;
-                        batch.push_back(*it);
-                        it = sv->waiting.erase(it);
-                    } else {
-                        ++it;
-                    }
-                }
-                if (batch.empty()) break;  // over budget: wait for retirements
-                s.busy = true;
-                s.bytes = bytes;
-                s.reqs = batch;
-                s.t_start = now_ns();
-                sv->used_bytes += bytes;
-                for (auto &q : batch) sv->state[q->ticket] = 1;
-                sv->counters[2]++;
-                s.packed = true;
-                lk.unlock();
-                int rc = launch_packed(sv, s, batch);
-                lk.lock();
-                if (rc) {
-                    fail_slot(sv, s, rc);
-                    sv->cv_done.notify_all();
-                }
+            const bool fits = sv->used_bytes + head->footprint <= sv->o.hbm_budget_bytes || sv->used_bytes == 0;
+            std::vector<std::shared_ptr<Req>> batch;
+            size_t bytes = 0;
+            int kind;
+            if (small || !fits) {
+                // a large head over the budget waits for retirements; small
+                // requests behind it still run (their footprint is a table)
+                batch = take_small(sv, &bytes);
+                if (batch.empty()) break;
+                kind = SLOT_PACKED;
             } else {
-                if (sv->used_bytes + head->footprint > sv->o.hbm_budget_bytes && sv->used_bytes > 0) break;
-                sv->waiting.pop_front();
-                s.busy = true;
-                s.bytes = head->footprint;
-                s.reqs = {head};
-                s.t_start = now_ns();
-                sv->used_bytes += head->footprint;
-                sv->state[head->ticket] = 1;
-                sv->counters[3]++;
-                s.packed = false;
-                lk.unlock();
-                int rc = launch_large(sv, s, *head);
-                lk.lock();
-                if (rc) {
-                    fail_slot(sv, s, rc);
-                    sv->cv_done.notify_all();
-                }
+                batch = take_group(sv, &bytes);
+                kind = batch.size() > 1 ? SLOT_GROUP : SLOT_SINGLE;
+            }
+            s.busy = true;
+            s.bytes = bytes;
+            s.reqs = batch;
+            s.t_start = now_ns();
+            s.kind = kind;
+            sv->used_bytes += bytes;
+            for (auto &q : batch) sv->state[q->ticket] = 1;
+            if (kind == SLOT_PACKED) sv->counters[2]++;
+            if (kind == SLOT_SINGLE) sv->counters[3]++;
+            if (kind == SLOT_GROUP) sv->counters[7] += batch.size();
+            lk.unlock();
+            const uint64_t t_issue = now_ns();
+            int rc = kind == SLOT_PACKED  ? launch_packed(sv, s, batch)
+                     : kind == SLOT_GROUP ? launch_group(sv, s, batch)
+                                          : launch_large(sv, s, *batch[0]);
+            const uint64_t t_issued = now_ns();
+            lk.lock();
+            if (!sv->t_first) sv->t_first = t_issue;
+            sv->issue_ns += t_issued - t_issue;
+            sv->issues++;
+            if (rc) {
+                fail_slot(sv, s, rc);
+                sv->cv_done.notify_all();
             }
             sv->counters[4] = std::max<uint64_t>(sv->counters[4], sv->used_bytes);
         }
-        // (3) wait: briefly when work is in flight, otherwise until a submit
+        // (3) sleep until something changes: a submit, a cancel, shutdown or a
+        // slot's completion callback (bounded, in case a wake-up is missed)
         bool busy = false;
         for (auto &s : sv->slots) busy = busy || s.busy;
-        if (busy)
-            sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
-        else if (!sv->stop)
-            sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        sv->cv_work.wait_for(lk, busy ? std::chrono::milliseconds(2) : std::chrono::milliseconds(20),
+                             [&] { return sv->epoch != epoch0; });
     }
 }
 
@@ -473,6 +606,7 @@ extern "C" int qaoa_serve_submit(qaoa_server *sv, const naesat_instance *inst, i
         sv->waiting.push_back(q);
         sv->state[q->ticket] = 0;
         sv->counters[0]++;
+        sv->epoch++;
         *ticket = q->ticket;
     }
     sv->cv_work.notify_one();
@@ -542,11 +676,21 @@ extern "C" int qaoa_server_stats(qaoa_server *sv, uint64_t *counters) {
     return QAOA_OK;
 }
 
+extern "C" int qaoa_server_issue_time(qaoa_server *sv, uint64_t *issue_ns, uint64_t *issues, uint64_t *span_ns) {
+    if (!sv || !issue_ns || !issues || !span_ns) return set_error(QAOA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *issue_ns = sv->issue_ns;
+    *issues = sv->issues;
+    *span_ns = sv->t_first ? now_ns() - sv->t_first : 0;
+    return QAOA_OK;
+}
+
 extern "C" int qaoa_server_destroy(qaoa_server *sv) {
     if (!sv) return set_error(QAOA_EINVAL, "NULL argument");
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
+        sv->epoch++;
     }
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();

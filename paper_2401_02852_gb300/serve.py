@@ -77,8 +77,16 @@ class Server:
         c = (ctypes.c_uint64 * 8)()
         check(load().qaoa_server_stats(self._h, c))
         keys = ["submitted", "completed", "packed_launches", "single_launches", "peak_bytes", "cancelled", "errors",
-                "reserved"]
+                "grouped_requests"]
         return dict(zip(keys, (int(v) for v in c)))
+
+    def issue_time(self) -> dict:
+        """Host time spent issuing work and its share of the time since the first admission."""
+        ns, k, span = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(load().qaoa_server_issue_time(self._h, ctypes.byref(ns), ctypes.byref(k), ctypes.byref(span)))
+        return {"issue_s": ns.value * 1e-9, "issues": int(k.value), "span_s": span.value * 1e-9,
+                "issue_share": ns.value / span.value if span.value else None,
+                "mean_issue_us": ns.value / k.value / 1e3 if k.value else None}
 
     def close(self):
         if self._h:
@@ -111,9 +119,11 @@ def replay(server: Server, requests: Sequence, time_scale: float = 1.0, timeout_
     return out, wall
 
 
-def one_per_launch(requests: Sequence, dtype="c64", time_scale: float = 1.0):
+def one_per_launch(requests: Sequence, dtype="c64", time_scale: float = 1.0, flags: int = 0, half_above: int = 14):
     """Baseline on the same GPU: one request at a time, each its own cost-table
-    and evolution launches, in arrival order (queueing delay included)."""
+    and evolution launches, in arrival order (queueing delay included).  With
+    QAOA_Z2_HALF in ``flags`` the requests with n > ``half_above`` run on the
+    halved state, as a server with that flag runs its unpacked requests."""
     import torch
 
     from . import api
@@ -128,7 +138,8 @@ def one_per_launch(requests: Sequence, dtype="c64", time_scale: float = 1.0):
         if due > now:
             time.sleep(due - now)
         arrival = max(due, t0)
-        ps, nm = api.psucc_host(rq.instance, rq.gamma, rq.beta, dtype, work=work)
+        f = flags if rq.instance.n > half_above else flags & ~_lib.Z2_HALF
+        ps, nm = api.psucc_host(rq.instance, rq.gamma, rq.beta, dtype, flags=f, work=work)
         torch.cuda.synchronize()
         done = time.perf_counter()
         lat.append(done - arrival)

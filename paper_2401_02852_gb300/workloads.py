@@ -20,6 +20,7 @@ the library's C ABI.
 from __future__ import annotations
 
 import time
+from typing import Optional
 
 import numpy as np
 import torch
@@ -32,38 +33,81 @@ def _sync():
     torch.cuda.synchronize()
 
 
-def serve_workload(count: int = 20000, rate_hz: float = 200.0, n_range=(14, 26), p_range=(1, 20),
-                   n_streams: int = 4, seed: int = 0, baseline: bool = True, z2: bool = True) -> dict:
-    reqs = gen.serving_requests(count, rate_hz=rate_hz, n_range=n_range, p_range=p_range, seed=seed)
-    warm = gen.serving_requests(16, rate_hz=1e6, n_range=n_range, p_range=p_range, seed=seed + 1)
-    with serve.Server("c64", n_streams=n_streams, flags=api.Z2_HALF if z2 else 0) as s:
+def _serve_arms(reqs, warm, n_streams: int, z2: bool, baseline: bool) -> dict:
+    """One request stream through the native server and, optionally, one
+    request per launch on the same GPU, both on the same state layout."""
+    flags = api.Z2_HALF if z2 else 0
+    with serve.Server("c64", n_streams=n_streams, flags=flags) as s:
         for rq in warm:
             s.wait(s.submit(rq.instance, rq.gamma, rq.beta))
         res, wall = serve.replay(s, reqs)
         stats = s.stats()
+        issue = s.issue_time()
     lat = np.array([r.latency_s for r in res])
+    count = len(reqs)
     amp_layers = sum((1 << rq.instance.n) * rq.p for rq in reqs)
-    out = {"requests": count, "rate_hz": rate_hz, "n_range": list(n_range), "p_range": list(p_range),
-           "server_halved_state": z2,
-           "server": serve.latency_summary(lat, wall, count) | {"amp_layer_per_s": amp_layers / wall},
-           "server_stats": stats, "errors": int(sum(r.status != 0 for r in res))}
+    out = {"server": serve.latency_summary(lat, wall, count) | {"amp_layer_per_s": amp_layers / wall},
+           "server_stats": stats, "server_issue": issue, "errors": int(sum(r.status != 0 for r in res))}
     if baseline:
         work = {}
         for rq in warm:
             api.psucc_host(rq.instance, rq.gamma, rq.beta, "c64", work=work)
-        base_ps, base_lat, base_wall = serve.one_per_launch(reqs)
+        base_ps, base_lat, base_wall = serve.one_per_launch(reqs, flags=flags)
         out["one_per_launch"] = serve.latency_summary(base_lat, base_wall, count)
         ps = np.array([r.p_succ for r in res])
         bp = np.array(base_ps)
         mask = bp > 0
-        out["max_rel_diff_vs_one_per_launch"] = float(np.max(np.abs(ps[mask] - bp[mask]) / bp[mask])) if mask.any() else 0.0
+        out["max_rel_diff_vs_one_per_launch"] = (float(np.max(np.abs(ps[mask] - bp[mask]) / bp[mask]))
+                                                 if mask.any() else 0.0)
         out["speedup_inst_per_s"] = out["server"]["inst_per_s"] / out["one_per_launch"]["inst_per_s"]
         out["p99_ratio"] = out["one_per_launch"]["p99_ms"] / out["server"]["p99_ms"]
     return out
 
 
+def serve_workload(count: int = 20000, rate_hz: float = 200.0, n_range=(14, 26), p_range=(1, 20),
+                   n_streams: int = 4, seed: int = 0, baseline: bool = True, z2: bool = False) -> dict:
+    """The configured serving stream (Poisson arrivals).  Both arms use the same
+    state layout: the full state, or with ``z2`` the halved state for every
+    request above the packing limit (n > 14) in both."""
+    reqs = gen.serving_requests(count, rate_hz=rate_hz, n_range=n_range, p_range=p_range, seed=seed)
+    warm = gen.serving_requests(16, rate_hz=1e6, n_range=n_range, p_range=p_range, seed=seed + 1)
+    out = {"requests": count, "rate_hz": rate_hz, "n_range": list(n_range), "p_range": list(p_range),
+           "state_layout": "halved (both arms)" if z2 else "full (both arms)"}
+    out.update(_serve_arms(reqs, warm, n_streams, z2, baseline))
+    return out
+
+
+def serve_rate_sweep(rates=(200.0, 1000.0, 2000.0, 5000.0, 20000.0), count: int = 3000, n_range=(14, 26),
+                     p_range=(1, 20), n_streams: int = 4, z2: bool = False) -> dict:
+    """Offered rates from light load to past saturation (the same request mix at
+    each rate, its own seeded stream): instances/s, p50 and p99 of the server
+    and of one request per launch."""
+    warm = gen.serving_requests(16, rate_hz=1e6, n_range=n_range, p_range=p_range, seed=99)
+    rows = []
+    for i, rate in enumerate(rates):
+        reqs = gen.serving_requests(count, rate_hz=rate, n_range=n_range, p_range=p_range, seed=100 + i)
+        r = _serve_arms(reqs, warm, n_streams, z2, True)
+        rows.append({"offered_per_s": rate, "requests": count,
+                     "server": {k: r["server"][k] for k in ("inst_per_s", "p50_ms", "p99_ms")},
+                     "one_per_launch": {k: r["one_per_launch"][k] for k in ("inst_per_s", "p50_ms", "p99_ms")},
+                     "speedup_inst_per_s": r["speedup_inst_per_s"],
+                     "grouped_requests": r["server_stats"]["grouped_requests"],
+                     "packed_launches": r["server_stats"]["packed_launches"],
+                     "single_launches": r["server_stats"]["single_launches"],
+                     "server_issue_share": r["server_issue"]["issue_share"],
+                     "server_mean_issue_us": r["server_issue"]["mean_issue_us"],
+                     "max_rel_diff_vs_one_per_launch": r["max_rel_diff_vs_one_per_launch"], "errors": r["errors"]})
+    return {"state_layout": "halved (both arms)" if z2 else "full (both arms)", "n_range": list(n_range),
+            "p_range": list(p_range), "rates": rows}
+
+
 def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 200, lr: float = 0.01,
-                  fd_instances: int = 2, seed_tag: str = "grad-cfg", checkpoint=None) -> dict:
+                  fd_instances: int = 2, seed_tag: str = "grad-cfg", checkpoint=None,
+                  reference: Optional[dict] = None) -> dict:
+    """Batched adjoint gradients; ``reference`` (optional) holds stored FP64
+    results for the first instances ({"instances": [{"index", "attempt",
+    "p_succ", "dgamma", "dbeta"}, ...]}) that the complex64 and complex128
+    gradients are compared with."""
     m = gen.clause_count(n, 8.0)
     insts = []
     for i in range(batch):
@@ -121,10 +165,28 @@ def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 
                    "c64_vs_c128_max_abs_over_max_grad": float(max(np.max(np.abs(dg[i] - dg128)),
                                                                   np.max(np.abs(db[i] - db128))) / scale),
                    "c64_psucc_rel_err_vs_c128": abs(ps[i] - ps128) / ps128})
+    vs_ref = []
+    for rec in (reference or {}).get("instances", []):
+        i = int(rec["index"])
+        if i >= batch or insts[i].seed_key[-1] != rec["attempt"]:
+            continue
+        rdg, rdb = np.array(rec["dgamma"]), np.array(rec["dbeta"])
+        scale = max(np.max(np.abs(rdg)), np.max(np.abs(rdb)))
+        ps128, dg128, db128 = api.grad(n, costs[i].contiguous(), m, g0, b0, "c128")
+        vs_ref.append({"instance": i,
+                       "c64_grad_max_abs_err_over_max_grad": float(max(np.max(np.abs(dg[i] - rdg)),
+                                                                       np.max(np.abs(db[i] - rdb))) / scale),
+                       "c128_grad_max_abs_err_over_max_grad": float(max(np.max(np.abs(dg128 - rdg)),
+                                                                        np.max(np.abs(db128 - rdb))) / scale),
+                       "c64_psucc_rel_err": abs(float(ps[i]) - rec["p_succ"]) / rec["p_succ"],
+                       "c128_psucc_rel_err": abs(ps128 - rec["p_succ"]) / rec["p_succ"]})
     del work
     torch.cuda.empty_cache()
     t0 = time.perf_counter()
-    g1, b1, trace = train.train_angles(costs, n, m, g0, b0, steps=adam_steps, lr=lr, checkpoint=checkpoint)
+    if adam_steps > 0:
+        g1, b1, trace = train.train_angles(costs, n, m, g0, b0, steps=adam_steps, lr=lr, checkpoint=checkpoint)
+    else:
+        g1, b1, trace = g0, b0, [(0, float(np.mean(np.log(np.maximum(ps, 1e-300)))))]
     _sync()
     t_adam = time.perf_counter() - t0
     # one gradient = forward (p layers) + reverse sweep (p layers on two states)
@@ -143,7 +205,7 @@ def grad_workload(batch: int = 256, n: int = 22, p: int = 20, adam_steps: int = 
             v["frac_of_measured_peak"] = v["GBps"] / peak
     return {"batch": batch, "n": n, "m": m, "p": p, "grad_seconds": t_grad, "roofline_by_kind": roof,
             "grad_amp_layer_per_s_forward_equiv": amp_layers / t_grad, "mean_psucc_initial": float(np.mean(ps)),
-            "fd_checks": fd, "adam_steps": adam_steps, "adam_seconds": t_adam,
+            "fd_checks": fd, "vs_oracle": vs_ref, "adam_steps": adam_steps, "adam_seconds": t_adam,
             "objective_first": trace[0][1], "objective_last": trace[-1][1],
             "trace_every_20": [t for t in trace if t[0] % 20 == 0 or t[0] == len(trace) - 1],
             "gamma_final": list(map(float, g1)), "beta_final": list(map(float, b1))}

@@ -46,6 +46,32 @@ def test_results_same_alone_and_in_mix():
             assert r.n_sol == alone[j].n_sol
 
 
+@pytest.mark.parametrize("z2", [False, True])
+def test_results_same_alone_and_batched(z2):
+    """Requests of one shape (n, m, p, angles) that wait together run as one
+    batched pass sequence; each result equals the request's result alone, bit
+    for bit, and the batched runs match the oracle."""
+    from paper_2401_02852_gb300._lib import Z2_HALF
+    flags = Z2_HALF if z2 else 0
+    same = [_req(17, 5, 200 + i, tag="grp") for i in range(6)] + [_req(20, 3, 300 + i, tag="grp") for i in range(3)]
+    with Server("c64", n_streams=1, flags=flags) as s:
+        alone = [s.wait(s.submit(*r)) for r in same]
+        assert s.stats()["grouped_requests"] == 0
+        blocker = s.submit(*_req(24, 20, 0, tag="grp-block"))  # holds the only slot while the others queue
+        tickets = [s.submit(*r) for r in same]
+        assert s.wait(blocker, 300).status == 0
+        grouped = [s.wait(t, 300) for t in tickets]
+        st = s.stats()
+    assert st["grouped_requests"] >= 6, st
+    for a, b in zip(alone, grouped):
+        assert b.status == 0 and (b.p_succ, b.norm, b.n_sol, b.max_cost) == (a.p_succ, a.norm, a.n_sol, a.max_cost)
+    for (inst, g, b), r in zip(same[:2] + same[6:7], grouped[:2] + grouped[6:7]):
+        cost, sol, _ = oracle.cost_table(inst.n, inst.var, inst.neg)
+        ref_ps, _ = oracle.success_prob(inst.n, cost, oracle.evolve(inst.n, cost, g, b))
+        assert r.n_sol == sol
+        assert abs(r.p_succ - ref_ps) <= 1e-4 * ref_ps + 1e-300
+
+
 @pytest.mark.parametrize("n,p", [(10, 3), (14, 6), (16, 4), (19, 2)])
 def test_serving_matches_oracle(n, p):
     inst, g, b = _req(n, p, 7, tag="srv-orc")
