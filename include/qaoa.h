@@ -58,8 +58,9 @@ extern "C" {
 /* Mixer sign.  The paper writes U_B(beta) = exp(-i beta H_B) in Sec. 2.1 but
  * uses U_B(beta) = exp(+i beta sum_j X_j) = prod_j [cos(beta) I + i sin(beta)
  * X_j] for the NAE problem (Sec. "Efficient Classical Simulation", Appendix
- * A.3, "due to the problem being recast as a minimisation").  The default is
- * the latter.  QAOA_MIXER_RX2B selects exp(-i beta sum_j X_j) = prod_j RX(2 beta). */
+ * A.3: the sign flips because the problem is posed as a minimisation).  The
+ * default is the latter.  QAOA_MIXER_RX2B selects exp(-i beta sum_j X_j) =
+ * prod_j RX(2 beta). */
 #define QAOA_MIXER_PAPER 0x0
 #define QAOA_MIXER_RX2B 0x1
 
@@ -175,8 +176,15 @@ int qaoa_success_prob(int n, const uint8_t *d_cost, const void *d_state, int dty
  *   [1, 32] fits; other n return QAOA_ERANGE.  No cudaMalloc, cudaFree or other
  *   allocating routine is called; the result is copied into a local host buffer.
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current, which also loads the
+ *   library's device code on that device if nothing of the library has run
+ *   there yet (CUDA loads modules lazily by default): that load allocates the
+ *   module and its fixed array.  So make one warm-up call per device at
+ *   start-up, before the caller's own allocator reserves the device and before
+ *   any stream capture (or run with CUDA_MODULE_LOADING=EAGER, which loads
+ *   the module when the context is created).  The address is kept for the
+ *   life of the process: a device reset (cudaDeviceReset) between calls is
+ *   not supported.
  *   Sharing: all calls share the array, which keeps the last call's contents;
  *   every entry a call reads is written earlier in the same call, so nothing
  *   needs clearing.  Calls whose work overlaps on the GPU (other streams or
@@ -250,14 +258,18 @@ int qaoa_grad_batch(int batch, int n, const uint8_t *d_costs, int m_max, int p, 
  * n (1..max_n) and depth arrive through qaoa_serve_submit; each is admitted
  * when its footprint fits the budget and a slot is free, packed with other
  * small-n requests into one launch when n <= small_n_max, and otherwise run as
- * its own multi-pass evolution on one of the streams.  Results are read with
- * qaoa_serve_poll / qaoa_serve_wait.  (Not in the paper: a serving pattern
- * around its simulation.) */
+ * a multi-pass evolution on one of the streams, batched with the waiting
+ * requests of the same shape (same n, m, p and angles: one pass plan and one
+ * set of phase tables), up to max_batch.  Small requests behind a large one
+ * that is over the budget are still admitted.  Results are read with
+ * qaoa_serve_poll / qaoa_serve_wait; each request's result is the same whether
+ * it runs alone, packed or batched (its arithmetic depends on its own inputs
+ * only).  (Not in the paper: a serving pattern around its simulation.) */
 typedef struct qaoa_server qaoa_server;
 
 typedef struct {
     size_t hbm_budget_bytes; /* admission budget for resident tables + states (0 = 50% of free) */
-    int max_batch;           /* max requests per packed small-n launch (0 = 256)               */
+    int max_batch;           /* max requests per packed small-n launch or same-shape batch (0 = 256) */
     int n_streams;           /* CUDA streams for large requests (0 = 4)                       */
     int dtype;               /* QAOA_C64 or QAOA_C128                                          */
     int small_n_max;         /* n at or below which requests are packed (0 = default)         */
@@ -288,8 +300,15 @@ int qaoa_serve_poll(qaoa_server *s, uint64_t ticket, qaoa_result *out);
 int qaoa_serve_wait(qaoa_server *s, uint64_t ticket, qaoa_result *out, double timeout_s);
 /* Cancels a request that has not started; QAOA_OK or QAOA_PENDING if running. */
 int qaoa_serve_cancel(qaoa_server *s, uint64_t ticket);
-/* Counters: submitted, completed, packed launches, single launches, peak bytes. */
+/* Counters: submitted, completed, packed launches, single launches, peak bytes,
+ * cancelled, errors, requests run in same-shape batches of two or more. */
 int qaoa_server_stats(qaoa_server *s, uint64_t *counters /* [8] */);
+/* Host time the scheduler thread has spent issuing work (staging uploads,
+ * stream-ordered allocations, kernel launches and result copies, for all
+ * slots), the number of issues (one per packed batch, same-shape batch or
+ * single request) and the time since the first admission, all in ns: the
+ * share of the scheduler's time that launches take. */
+int qaoa_server_issue_time(qaoa_server *s, uint64_t *issue_ns, uint64_t *issues, uint64_t *span_ns);
 /* Drains running work, joins the scheduler, frees device memory. */
 int qaoa_server_destroy(qaoa_server *s);
 

@@ -149,7 +149,12 @@ __global__ void __launch_bounds__(PT, sizeof(R) == 4 ? 2 : 1) adj_kernel(const _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tp = reinterpret_cast<V *>(smem_raw);
     V *tl = tp + G::TILE_ELEMS;
-    uint8_t *scs = reinterpret_cast<uint8_t *>(tl + G::TILE_ELEMS);  // phase passes: 2 x 2^T cost bytes
+    // phase passes: two dense cost-byte buffers.  (The forward high passes pad
+    // theirs so that the cost loads in mapping 4 take one wavefront instead of
+    // two; here the extra per-thread offset made the fused kernels, which hold
+    // both states in registers, spill, so the backward passes keep the dense
+    // layout and its second wavefront.)
+    uint8_t *scs = reinterpret_cast<uint8_t *>(tl + G::TILE_ELEMS);
     V *stab = reinterpret_cast<V *>(scs + (PH ? (2 << T) : 0));
     if (PH) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += PT) {

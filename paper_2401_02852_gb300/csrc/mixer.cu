@@ -139,7 +139,7 @@ constexpr bool is_df() {
     return std::is_same<R, dfloat>::value;
 }
 
-template <typename R, int LO, int ROW, bool Z2, bool RED>
+template <typename R, int LO, int ROW, bool Z2, bool RED, bool PADC>
 __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename Cx<R>::V *sp, const uint8_t *sc,
                                            typename Cx<R>::V *sa, uint32_t gstride, bool mirror, bool reduce,
                                            double acc[2]) {
@@ -174,12 +174,13 @@ __device__ __forceinline__ void store_tile(const typename Cx<R>::V *v, typename 
         // of each |v|^2), then everything above the thread in FP64.
         PairwiseSum<NR, P> ps, nm;
         const uint32_t tid = threadIdx.x;
+        const uint32_t cb = PADC ? cost_base<Cx<R>, LO>(tid) : 0u;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const P w = amp_prob(v[r]);
             nm.add(r, w);
             const uint32_t u = tile_elem<Cx<R>, LO>(tid, r);
-            const bool sol = sc[Z2 ? land<Cx<R>::T>(u) : u] == 0;
+            const bool sol = sc[PADC ? cb + Cx<R>::cidx((uint32_t)r << LO) : (Z2 ? land<Cx<R>::T>(u) : u)] == 0;
             ps.add(r, sol ? w : P(0));
             if (sa) sa[off(r)] = sol ? v[r] : zero_amp<V>();
         }
@@ -264,7 +265,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         if (Z2)
             issue_tile_z2<R>(st, cs, bb, M - bb - (H - 1), need_s, need_c, tile, scb);
         else
-            issue_tile<Cx<R>>(st, cs, bb, row, a.lo, need_s, need_c, tile, scb);
+            issue_tile<Cx<R>, !LOW>(st, cs, bb, row, a.lo, need_s, need_c, tile, scb);
     };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     const uint32_t tiles = (uint32_t)a.tiles;
@@ -285,7 +286,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     cp_async_commit();
     for (uint32_t i = 0; t < tiles; ++i, t = tile_at(i)) {
         const int b = i & 1;
-        uint8_t *sc = scs + ((size_t)b << T);
+        uint8_t *sc = scs + (size_t)b * G::CS_BYTES;
         const uint32_t base = base_of(t);
         const uint32_t tn = tile_at(i + 1);
         // Once the tile's last exchange is read out the buffer is free: copy the
@@ -293,37 +294,41 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         // while this tile finishes its last round and its stores.
         auto prefetch = [&]() {
             __syncthreads();
-            if (tn < tiles) issue(tn, scs + ((size_t)(b ^ 1) << T));
+            if (tn < tiles) issue(tn, scs + (size_t)(b ^ 1) * G::CS_BYTES);
             cp_async_commit();
         };
         cp_async_wait_all();  // this tile's copies are done
         __syncthreads();
         V v[NR];
+        const uint32_t cbl = LOW ? 0u : cost_base<G, LD>(tid);  // high passes: padded cost bytes
 #pragma unroll
         for (int r = 0; r < NR; ++r) {  // load mapping on the dense buffer: consecutive lanes, no conflicts
             const uint32_t u0 = tile_elem<G, LD>(tid, r);
             const uint32_t u = Z2 ? land<T>(u0) : u0;
+            const uint8_t c = LOW ? sc[u] : sc[cbl + G::cidx((uint32_t)r << LD)];
             if (MODE == MODE_INIT)
-                v[r] = stab[sc[u]];
+                v[r] = stab[c];
             else if (MODE == MODE_PHASE)
-                v[r] = cmul(tile[u], stab[sc[u]]);
+                v[r] = cmul(tile[u], stab[c]);
             else
                 v[r] = tile[u];
         }
         if (MODE == MODE_FUSED) {
             rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, NoHook());
 #pragma unroll
-            for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[tile_elem<G, LC>(tid, r)]]);
+            const uint32_t cb = cost_base<G, LC>(tid);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[cb + G::cidx((uint32_t)r << LC)]]);
             rounds_down<G, LOW, UA2>(v, tile, active, a.A2, a.B2, prefetch);
-            store_tile<R, LD, row, false, false>(v, st + (base + ld_t), sc, nullptr, gstride, false, false, acc);
+            store_tile<R, LD, row, false, false, !LOW>(v, st + (base + ld_t), sc, nullptr, gstride, false, false, acc);
         } else {
             rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, prefetch);
             if (Z2) {  // the mirror half stores in descending order
                 const uint32_t ul0 = z_u0 & (H - 1);
                 V *sp = z_mir ? st + (M - base - ul0) : st + (base + ul0);
-                store_tile<R, LC, row, true, RED>(v, sp, sc, nullptr, gstride, z_mir, red, acc);
+                store_tile<R, LC, row, true, RED, false>(v, sp, sc, nullptr, gstride, z_mir, red, acc);
             } else {
-                store_tile<R, LC, row, false, RED>(v, st + (base + st_t), sc, adj ? adj + (base + st_t) : nullptr,
+                store_tile<R, LC, row, false, RED, !LOW>(v, st + (base + st_t), sc, adj ? adj + (base + st_t) : nullptr,
                                                    gstride, false, red, acc);
             }
         }
@@ -346,7 +351,7 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
 }
 
 // Two CTAs per SM, persistent over tiles: one (padded) tile buffer, two
-// cost-byte buffers, then the phase table.
+// cost-byte buffers (padded in high passes), then the phase table.
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT, bool Z2 = false, bool RED = false,
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constan
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
     uint8_t *scs = reinterpret_cast<uint8_t *>(tile + Cx<R>::TILE_ELEMS);
-    V *stab = reinterpret_cast<V *>(scs + (2 << T));
+    V *stab = reinterpret_cast<V *>(scs + 2 * Cx<R>::CS_BYTES);
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) stab[i] = i <= a.m ? tab.t[i] : zero_amp<V>();
         __syncthreads();
@@ -587,8 +592,7 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 // the phase table (modes that apply a phase).
 template <typename R>
 static size_t pass_smem(bool phase, int m) {
-    const size_t T = size_t(1) << Cx<R>::T;
-    return sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS + 2 * T +
+    return sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS + 2 * (size_t)Cx<R>::CS_BYTES +
            (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
@@ -1125,13 +1129,17 @@ extern "C" int qaoa_success_prob_noalloc(int n, const uint8_t *d_cost, const voi
     const int grid = (int)(chunks < g ? chunks : g);
     double *d_part = scr;                             // [grid][2], all written before they are read
     double *d_res = scr + 2 * NOALLOC_MAX_BLOCKS;     // [2]
+    profile_before(K_PSUCC, stream);
     if (dtype == QAOA_C64)
         psucc_kernel<float><<<grid, PT, 0, stream>>>(reinterpret_cast<const float2 *>(d_state), d_cost, n, d_part);
     else
         psucc_kernel<double><<<grid, PT, 0, stream>>>(reinterpret_cast<const double2 *>(d_state), d_cost, n, d_part);
-    QAOA_CUDA_TRY(cudaGetLastError());
+    rc = profile_after(K_PSUCC, stream);  // counts the launch, checks its status
+    if (rc) return rc;
+    profile_before(K_REDUCE, stream);
     reduce_partials_kernel<<<1, PT, 0, stream>>>(d_part, grid, 2, d_res);
-    QAOA_CUDA_TRY(cudaGetLastError());
+    rc = profile_after(K_REDUCE, stream);
+    if (rc) return rc;
     double h[2];  // pageable host copy: the runtime stages it, nothing is allocated here
     QAOA_CUDA_TRY(cudaMemcpyAsync(h, d_res, sizeof h, cudaMemcpyDeviceToHost, stream));
     QAOA_CUDA_TRY(cudaStreamSynchronize(stream));

@@ -80,7 +80,29 @@ struct Geo {
     static constexpr int PADSH = RB_;
     static constexpr int TILE_ELEMS = (1 << T_) + (1 << (T_ - RB_));
     __host__ __device__ static constexpr uint32_t swz(uint32_t u) { return u + (u >> PADSH); }
+    // Cost bytes of a high-pass tile: 16 spare bytes after every 2^(4 + RB).  In
+    // the passes' last mapping (4) lanes 0..15 read 16 consecutive bytes and
+    // lanes 16..31 the 16 bytes 2^(4 + RB) further on, which the dense layout
+    // puts in the same four banks (one extra wavefront per load); the padding
+    // moves them to the next four.  The load mapping reads 32 consecutive bytes
+    // inside one period either way.  Low passes keep the dense layout.
+    static constexpr int CPAD = 4 + RB_;
+    static constexpr int CS_BYTES = (1 << T_) + ((1 << T_) >> RB_);  // one cost buffer, padded
+    // Additive over disjoint bit fields, so a mapping's cost index is the
+    // thread part's plus a compile-time constant per register.
+    __host__ __device__ static constexpr uint32_t cidx(uint32_t u) { return u + ((u >> CPAD) << 4); }
 };
+
+// The thread's cost bytes in mapping LO on the padded layout: register r's
+// byte is at sc[returned offset + G::cidx(r << LO)] (a compile-time offset).
+// The offset passes through an opaque asm, so it is formed where it is used
+// instead of being kept live across the tile loop.
+template <typename G, int LO>
+__device__ __forceinline__ uint32_t cost_base(uint32_t tid) {
+    uint32_t o = G::cidx((tid & ((1u << LO) - 1u)) | ((tid >> LO) << (LO + G::RB)));
+    asm volatile("" : "+r"(o));
+    return o;
+}
 
 // Forward geometry: 64 KiB tiles, 256 threads; complex64 with 32 amplitudes
 // per thread, complex128 with 16.
@@ -341,9 +363,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // (the tile's rows of 2^row amplitudes are whole numbers of chunks) and, when
 // needed, its cost bytes (one 16-byte chunk per row of 16 amplitudes).  Chunk q
 // of the tile lands at byte 16 q of the buffer, i.e. tile element u sits at
-// buf[u]; thread tid takes chunks tid + PT j, whose addresses are a thread
-// base plus j times a stride.  Indices inside one instance fit in 32 bits.
-template <typename G>
+// buf[u] (with PADC the cost byte of u at sc[G::cidx(u)]); thread tid takes
+// chunks tid + PT j, whose addresses are a thread base plus j times a stride.
+// Indices inside one instance fit in 32 bits.
+template <typename G, bool PADC = false>
 __device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_t *cs, uint32_t base, int row, int lo,
                                            bool state, bool cost, typename G::V *buf, uint8_t *sc) {
     using V = typename G::V;
@@ -367,7 +390,10 @@ __device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_
         const uint32_t off0 = base + elem_offset32(16u * tid, row, lo);
         const uint32_t step = elem_offset32(16u * NT, row, lo);
 #pragma unroll
-        for (int j = 0; j < CCH; ++j) cp_async16(sc + 16 * (tid + NT * j), cs + (off0 + step * j));
+        for (int j = 0; j < CCH; ++j) {
+            const uint32_t q = tid + NT * j;  // 16-byte chunk q: bytes [16 q, 16 q + 16) of the tile
+            cp_async16(sc + 16 * q + (PADC ? 16 * (q >> G::RB) : 0), cs + (off0 + step * j));
+        }
     }
 }
 

@@ -12,7 +12,7 @@ Phase Transitions" for F_k(n, m)):
   variant is ``poisson_m=True``);
 * each clause draws k *distinct* variables uniformly (a uniform k-subset in a
   uniformly random order), clauses independently of each other (duplicates
-  across clauses allowed: "with replacement");
+  across clauses allowed: the clauses are drawn with replacement);
 * each literal is negated independently with probability 1/2.
 
 The paper's own evaluation draws CNF(n, k, r_hat_k) with m ~ Poisson(r_hat_k n)
