@@ -90,7 +90,10 @@ def test_replay_and_counters():
     with Server("c64", n_streams=2) as s:
         res, wall = replay(s, reqs)
         st = s.stats()
+        it = s.issue_time()
     assert st["submitted"] == st["completed"] == 60 and st["errors"] == 0
+    launches = st["packed_launches"] + st["single_launches"] + (1 if st["grouped_requests"] else 0)
+    assert it["issues"] >= launches and 0 < it["issue_s"] < it["span_s"]
     assert all(r.status == 0 and r.t_submit_ns <= r.t_start_ns <= r.t_done_ns for r in res)
     assert wall > 0
 
