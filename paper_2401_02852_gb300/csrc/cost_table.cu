@@ -24,6 +24,12 @@
 // planes do (m <= 8191).  Only the counts <= 255 go into the table; a larger
 // one makes the call fail with the exact maximum.
 //
+// Global-flip symmetry.  Flipping every bit of x flips every literal, so a
+// clause's literals stay all equal or not: C(not x) = C(x) (Sec. 2.2).  The
+// complement of x = 32 X + b is 32 (W - 1 - X) + (31 - b) (W = 2^(n - 5)
+// words), so a full table is counted on its lower half only: each counted
+// word is written twice, the second time byte-reversed at word W - 1 - X.
+//
 // Clause filtering.  A block takes 512 consecutive words at a time, so the
 // variables >= 14 (SUB_BITS) are constant over them.  A clause whose literals
 // on those variables are neither all true nor all false is violated nowhere in
@@ -49,6 +55,7 @@ static_assert(QAOA_MAX_M < (1 << NPL_LARGE), "counts must fit the planes");
 
 struct CostParams {
     int n, m;
+    int mirror;  // count the lower half, write both (full tables, n >= 6)
     ClauseRec rec[CT_PARAM_M];
 };
 
@@ -155,9 +162,11 @@ __device__ __forceinline__ void planes_to_bytes(const uint32_t *planes, uint32_t
 }
 
 // Writes the 32 counts of word X (bytes) and folds its solution count and max.
+// With `mirror` (n >= 6) the same counts also go, byte-reversed, to the
+// complement word W - 1 - X, and they count twice.
 template <int NPL>
 __device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t planes[NPL], uint8_t *cost,
-                                          unsigned long long &nsol, uint32_t &mx) {
+                                          unsigned long long &nsol, uint32_t &mx, bool mirror) {
     const uint32_t valid = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
     uint32_t bytes[8];
     planes_to_bytes(planes, bytes);
@@ -168,7 +177,7 @@ __device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t plan
         any |= planes[q];
         if (q >= 8) over |= planes[q];
     }
-    nsol += __popc(~any & valid);
+    nsol += (mirror ? 2u : 1u) * __popc(~any & valid);
     over &= valid;
     uint32_t bm = 0;
     if (n >= 5) {
@@ -191,6 +200,14 @@ __device__ __forceinline__ void emit_word(int n, uint64_t X, const uint32_t plan
         uint4 *dst = reinterpret_cast<uint4 *>(cost + 32 * X);
         dst[0] = make_uint4(bytes[0], bytes[1], bytes[2], bytes[3]);
         dst[1] = make_uint4(bytes[4], bytes[5], bytes[6], bytes[7]);
+        if (mirror) {  // byte 31 - b of the complement word holds the count of byte b
+            const uint64_t Xm = (1ull << (n - 5)) - 1ull - X;
+            uint4 *dm = reinterpret_cast<uint4 *>(cost + 32 * Xm);
+            dm[0] = make_uint4(__byte_perm(bytes[7], 0, 0x0123), __byte_perm(bytes[6], 0, 0x0123),
+                               __byte_perm(bytes[5], 0, 0x0123), __byte_perm(bytes[4], 0, 0x0123));
+            dm[1] = make_uint4(__byte_perm(bytes[3], 0, 0x0123), __byte_perm(bytes[2], 0, 0x0123),
+                               __byte_perm(bytes[1], 0, 0x0123), __byte_perm(bytes[0], 0, 0x0123));
+        }
     } else {
         for (uint32_t b = 0; b < (1u << n); ++b) cost[b] = (uint8_t)((bytes[b >> 2] >> (8 * (b & 3))) & 0xFFu);
     }
@@ -241,8 +258,9 @@ __device__ __forceinline__ int filter_clauses(uint32_t base, int m, const uint4 
 // time.
 template <int NPL>
 __device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *recs, uint4 *alive, int *acount,
-                                                uint8_t *cost, unsigned long long *stats) {
-    const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
+                                                uint8_t *cost, unsigned long long *stats, bool mirror) {
+    mirror = mirror && n >= 6;  // the lower half is then a whole number of words
+    const uint64_t words = n >= 5 ? (1ull << (n - 5)) >> (mirror ? 1 : 0) : 1ull;  // words counted
     const uint64_t steps = (words + SUB_WORDS - 1) / SUB_WORDS;
     unsigned long long nsol = 0;
     uint32_t mx = 0;
@@ -260,8 +278,8 @@ __device__ __forceinline__ void cost_table_body(int n, int m, const uint4 *recs,
             uint32_t p0[NPL], p1[NPL];
             c0.planes(p0);
             c1.planes(p1);
-            emit_word<NPL>(n, X0, p0, cost, nsol, mx);
-            if (X1 < words) emit_word<NPL>(n, X1, p1, cost, nsol, mx);
+            emit_word<NPL>(n, X0, p0, cost, nsol, mx, mirror);
+            if (X1 < words) emit_word<NPL>(n, X1, p1, cost, nsol, mx, mirror);
         }
     }
     // warp then block reduction, one atomic pair per block
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(CT_THREADS) cost_table_kernel(const __grid_con
         srec[i] = make_uint4(r.hi_mask, r.hi_neg, r.all_true, r.all_false);
     }
     __syncthreads();
-    cost_table_body<NPL_SMALL>(prm.n, prm.m, srec, alive, &acount, cost, stats);
+    cost_table_body<NPL_SMALL>(prm.n, prm.m, srec, alive, &acount, cost, stats, prm.mirror != 0);
 }
 
 // Batched tables.  With ns == nullptr every instance has n qubits and its table
@@ -313,7 +331,7 @@ template <int NPL>
 __global__ void __launch_bounds__(CT_THREADS) cost_table_batch_kernel(int n, const int *ns, const uint64_t *offs,
                                                                       const ClauseRec *recs, const int *ms,
                                                                       int m_stride, uint8_t *costs,
-                                                                      unsigned long long *stats) {
+                                                                      unsigned long long *stats, int mirror) {
     static_assert(sizeof(ClauseRec) == sizeof(uint4), "a clause record is one 16-byte load");
     __shared__ uint4 srec[CT_CHUNK];
     __shared__ uint4 alive[CT_CHUNK];
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(CT_THREADS) cost_table_batch_kernel(int n, con
     }
     const int ni = ns ? ns[inst] : n;
     uint8_t *dst = ns ? costs + offs[inst] : costs + ((size_t)inst << n);
-    cost_table_body<NPL>(ni, m, src, alive, &acount, dst, stats + 2 * inst);
+    cost_table_body<NPL>(ni, m, src, alive, &acount, dst, stats + 2 * inst, mirror != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -391,17 +409,18 @@ static int grid_for(uint64_t words, int batch) {
 
 int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d_offs, const ClauseRec *d_recs,
                             const int *d_m, int m_stride, uint8_t *d_costs, unsigned long long *d_stats,
-                            cudaStream_t stream) {
-    const uint64_t words = n >= 5 ? (1ull << (n - 5)) : 1ull;
+                            cudaStream_t stream, bool mirror) {
+    const uint64_t words = n >= 5 ? (1ull << (n - 5)) >> (mirror && n >= 6 ? 1 : 0) : 1ull;
     const int gx = grid_for(words, batch);
     if (gx < 0) return QAOA_ECUDA;
+    const int mi = mirror ? 1 : 0;
     profile_before(K_COST_TABLE, stream);
     if (m_stride <= CT_PARAM_M)
         cost_table_batch_kernel<NPL_SMALL><<<dim3(gx, batch), CT_THREADS, 0, stream>>>(n, d_ns, d_offs, d_recs, d_m,
-                                                                                     m_stride, d_costs, d_stats);
+                                                                                     m_stride, d_costs, d_stats, mi);
     else
         cost_table_batch_kernel<NPL_LARGE><<<dim3(gx, batch), CT_THREADS, 0, stream>>>(n, d_ns, d_offs, d_recs, d_m,
-                                                                                     m_stride, d_costs, d_stats);
+                                                                                     m_stride, d_costs, d_stats, mi);
     return profile_after(K_COST_TABLE, stream);
 }
 
@@ -420,14 +439,15 @@ int launch_cost_table_one(const naesat_instance *inst, uint8_t *d_cost, unsigned
         // pageable sources: the copies return once the data is staged
         QAOA_CUDA_TRY(cudaMemcpyAsync(d_rec, rec.data(), rec.size() * sizeof(ClauseRec), cudaMemcpyHostToDevice, stream));
         QAOA_CUDA_TRY(cudaMemcpyAsync(d_m, &inst->m, sizeof(int), cudaMemcpyHostToDevice, stream));
-        return launch_cost_table_batch(1, n, nullptr, nullptr, d_rec, d_m, inst->m, d_cost, d_stats, stream);
+        return launch_cost_table_batch(1, n, nullptr, nullptr, d_rec, d_m, inst->m, d_cost, d_stats, stream, !half);
     }
     std::vector<char> buf(sizeof(CostParams));
     CostParams *prm = reinterpret_cast<CostParams *>(buf.data());
     prm->n = n;
     prm->m = inst->m;
+    prm->mirror = (!half && n >= 6) ? 1 : 0;  // a full table: count its lower half
     encode_instance(inst, prm->rec);
-    const uint64_t words = prm->n >= 5 ? (1ull << (prm->n - 5)) : 1ull;
+    const uint64_t words = prm->n >= 5 ? (1ull << (prm->n - 5)) >> prm->mirror : 1ull;
     const int gx = grid_for(words, 1);
     if (gx < 0) return QAOA_ECUDA;
     profile_before(K_COST_TABLE, stream);
@@ -505,7 +525,8 @@ extern "C" int naesat_cost_table_batch(int batch, const naesat_instance *insts, 
     unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(dbase + rec_bytes + m_bytes);
     QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, stat_bytes, stream));
     rc = launch_cost_table_batch(batch, n, nullptr, nullptr, reinterpret_cast<const ClauseRec *>(dbase),
-                                 reinterpret_cast<const int *>(dbase + rec_bytes), m_stride, d_costs, d_stats, stream);
+                                 reinterpret_cast<const int *>(dbase + rec_bytes), m_stride, d_costs, d_stats, stream,
+                                 true);
     if (rc) return rc;
     unsigned long long *h_stats = reinterpret_cast<unsigned long long *>(hbase + rec_bytes + m_bytes);
     QAOA_CUDA_TRY(cudaMemcpyAsync(h_stats, d_stats, stat_bytes, cudaMemcpyDeviceToHost, stream));

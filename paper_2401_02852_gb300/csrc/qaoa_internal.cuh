@@ -166,10 +166,13 @@ int validate_instance(const naesat_instance *inst);
 // m per instance on the device, results into d_stats [batch][2] (uint64 n_sol,
 // uint64 max C) which must be zeroed first.  With d_ns == nullptr all
 // instances have n qubits and consecutive tables; otherwise instance b has
-// d_ns[b] <= n qubits and its table at d_costs + d_offs[b].
+// d_ns[b] <= n qubits and its table at d_costs + d_offs[b].  `mirror`: the
+// tables are full ones (2^n entries), counted on their lower half and
+// completed by the global-flip symmetry; false for the lower-half tables of
+// the halved state (n then counts their index bits).
 int launch_cost_table_batch(int batch, int n, const int *d_ns, const uint64_t *d_offs, const ClauseRec *d_recs,
                             const int *d_m, int m_stride, uint8_t *d_costs, unsigned long long *d_stats,
-                            cudaStream_t stream);
+                            cudaStream_t stream, bool mirror);
 // One table.  Up to 1023 clauses the records go as kernel parameters (no
 // staging); a longer list is copied to d_big (device, cost_table_big_bytes(m)
 // bytes, 16-byte aligned) and counted chunk by chunk.

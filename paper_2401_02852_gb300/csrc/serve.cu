@@ -221,7 +221,7 @@ static int launch_group(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<Re
     QAOA_CUDA_TRY(cudaMemsetAsync(d_stats, 0, (size_t)B * 2 * sizeof(unsigned long long), s.stream));
     if ((rc = launch_cost_table_batch(B, nb, nullptr, nullptr, reinterpret_cast<const ClauseRec *>(d + o_recs),
                                       reinterpret_cast<const int *>(d + o_m), m_stride, (uint8_t *)s.d_cost, d_stats,
-                                      s.stream)))
+                                      s.stream, !z2)))
         return rc;
     EvolveReq r{B, q0.n, table_top(q0.m), q0.p, dtype, sv->o.flags, (const uint8_t *)s.d_cost, s.d_state, nullptr,
                 q0.gamma.data(), q0.beta.data(), d_res};
@@ -317,7 +317,7 @@ static int launch_packed(qaoa_server *sv, Slot &s, std::vector<std::shared_ptr<R
     if ((rc = launch_cost_table_batch(B, max_n, reinterpret_cast<int *>(d + o_n), reinterpret_cast<uint64_t *>(d + o_off),
                                       reinterpret_cast<ClauseRec *>(d + o_recs), reinterpret_cast<int *>(d + o_m),
                                       m_stride, (uint8_t *)s.d_cost, reinterpret_cast<unsigned long long *>(d + o_stats),
-                                      s.stream)))
+                                      s.stream, true)))
         return rc;
     if ((rc = launch_small_batch(sv->o.dtype, B, reinterpret_cast<SmallJob *>(d + o_jobs),
                                  reinterpret_cast<double *>(d + o_tab), reinterpret_cast<double *>(d + o_coef), max_n,

@@ -2,9 +2,11 @@
 
 * ``serve``:  a Poisson stream of NAE-5-SAT requests (n ~ U{14..26},
   p ~ U{1..20}, r = 8, linear ramps) through the native serving loop, against
-  one request per launch on the same GPU;
+  one request per launch on the same GPU and the same state layout;
+  ``serve_rate_sweep`` repeats it at offered rates up to saturation;
 * ``grad``:   batched adjoint gradients (256 instances, n = 22, p = 20) checked
-  against central differences, then Adam on the shared angles;
+  against central differences and, when given, stored FP64 oracle gradients,
+  then Adam on the shared angles;
 * ``sweep``:  median 1/p_succ versus n and its fitted exponent, and the median
   running time (bitstrings sampled until one satisfies) beside 1/E[p_succ];
 * ``batch``:  100 small instances (n = 12, p = 5, complex128) in one launch;
