@@ -224,9 +224,14 @@ __device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const
     }
 }
 
-template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2, bool RED, int HROW, bool FULL>
+// NB = 1: one tile buffer per CTA, two CTAs per SM; the next tile's copies
+// start once the current tile's last exchange is read out.  NB = 3: three tile
+// (and cost) buffers, one CTA per SM; tile i + 2's copies are issued when tile
+// i starts, so two tiles are always in flight while one is computed (a
+// cp.async commit-group pipeline: wait_group 2 completes the oldest).
+template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2, bool RED, int HROW, bool FULL, int NB>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
-                                           typename Cx<R>::V *tile, uint8_t *scs) {
+                                           typename Cx<R>::V *tiles_buf, uint8_t *scs) {
     using G = Cx<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
@@ -260,13 +265,15 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     const uint32_t z_u0 = tile_elem<G, LC>(tid, 0);  // its bit T - 1 is a thread bit in every store mapping
     const bool z_mir = Z2 && (z_u0 >> (T - 1));
     auto base_of = [&](uint32_t tt) { return Z2 ? (tt << (T - 1)) : tile_base32(tt, row, a.lo, T); };
-    auto issue = [&](uint32_t tt, uint8_t *scb) {
+    auto issue = [&](uint32_t tt, V *tb, uint8_t *scb) {
         const uint32_t bb = base_of(tt);
         if (Z2)
-            issue_tile_z2<R>(st, cs, bb, M - bb - (H - 1), need_s, need_c, tile, scb);
+            issue_tile_z2<R>(st, cs, bb, M - bb - (H - 1), need_s, need_c, tb, scb);
         else
-            issue_tile<Cx<R>, !LOW>(st, cs, bb, row, a.lo, need_s, need_c, tile, scb);
+            issue_tile<Cx<R>, !LOW>(st, cs, bb, row, a.lo, need_s, need_c, tb, scb);
     };
+    auto tbuf = [&](int b) { return tiles_buf + (size_t)b * G::TILE_ELEMS; };
+    auto cbuf = [&](int b) { return scs + (size_t)b * G::CS_BYTES; };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     const uint32_t tiles = (uint32_t)a.tiles;
     // High passes that read both the state and the cost bytes take tiles in
@@ -282,22 +289,40 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         return grouped ? GT * (blockIdx.x + (i / GT) * gridDim.x) + (i % GT) : blockIdx.x + i * gridDim.x;
     };
     uint32_t t = tile_at(0);
-    if (t < tiles) issue(t, scs);
+    if (t < tiles) issue(t, tbuf(0), cbuf(0));
     cp_async_commit();
+    if (NB == 3) {
+        const uint32_t t1 = tile_at(1);
+        if (t1 < tiles) issue(t1, tbuf(1), cbuf(1));
+        cp_async_commit();
+    }
     for (uint32_t i = 0; t < tiles; ++i, t = tile_at(i)) {
-        const int b = i & 1;
-        uint8_t *sc = scs + (size_t)b * G::CS_BYTES;
+        const int b = NB == 3 ? (int)(i % 3u) : (int)(i & 1u);
+        V *tile = NB == 3 ? tbuf(b) : tbuf(0);
+        uint8_t *sc = cbuf(b);
         const uint32_t base = base_of(t);
         const uint32_t tn = tile_at(i + 1);
-        // Once the tile's last exchange is read out the buffer is free: copy the
-        // next tile into it (and its cost bytes into the other cost buffer)
-        // while this tile finishes its last round and its stores.
+        // NB = 1: once the tile's last exchange is read out the buffer is free:
+        // copy the next tile into it (and its cost bytes into the other cost
+        // buffer) while this tile finishes its last round and its stores.
         auto prefetch = [&]() {
-            __syncthreads();
-            if (tn < tiles) issue(tn, scs + (size_t)(b ^ 1) * G::CS_BYTES);
-            cp_async_commit();
+            if constexpr (NB == 1) {
+                __syncthreads();
+                if (tn < tiles) issue(tn, tbuf(0), cbuf(b ^ 1));
+                cp_async_commit();
+            }
         };
-        cp_async_wait_all();  // this tile's copies are done
+        if constexpr (NB == 3) {
+            // every thread is done with tile i - 1, whose buffers take tile i + 2
+            __syncthreads();
+            const uint32_t t2 = tile_at(i + 2);
+            const int b2 = (int)((i + 2) % 3u);
+            if (t2 < tiles) issue(t2, tbuf(b2), cbuf(b2));
+            cp_async_commit();
+            asm volatile("cp.async.wait_group 2;\n" ::: "memory");  // tile i's copies are done
+        } else {
+            cp_async_wait_all();  // this tile's copies are done
+        }
         __syncthreads();
         V v[NR];
         const uint32_t cbl = LOW ? 0u : cost_base<G, LD>(tid);  // high passes: padded cost bytes
@@ -315,7 +340,6 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         }
         if (MODE == MODE_FUSED) {
             rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, NoHook());
-#pragma unroll
             const uint32_t cb = cost_base<G, LC>(tid);
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[cb + G::cidx((uint32_t)r << LC)]]);
@@ -350,25 +374,27 @@ __host__ __device__ __forceinline__ int table_entries(int m) {
     return (e + 15) & ~15;
 }
 
-// Two CTAs per SM, persistent over tiles: one (padded) tile buffer, two
-// cost-byte buffers (padded in high passes), then the phase table.
+// Persistent over tiles.  NB = 1: two CTAs per SM, one (padded) tile buffer
+// and two cost-byte buffers each; NB = 3: one CTA per SM, three of each.  Then
+// the phase table.  Cost bytes are padded in high passes.
 // UA1 / UA2: butterfly forms (A = 1 or B = 1) of the pass's one or two layers,
 // chosen on the host per layer.
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, int NT, bool Z2 = false, bool RED = false,
-          int HROW = HIGH_ROW, bool FULL = true>
-__global__ void __launch_bounds__(Cx<R>::PT, 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
-                                                            const __grid_constant__ PhaseTab<R, NT> tab) {
+          int HROW = HIGH_ROW, bool FULL = true, int NB = 1>
+__global__ void __launch_bounds__(Cx<R>::PT, NB == 3 ? 1 : 2) pass_kernel(const __grid_constant__ PassArgs<R> a,
+                                                                          const __grid_constant__ PhaseTab<R, NT> tab) {
     using V = typename Cx<R>::V;
     constexpr int T = Cx<R>::T;
+    constexpr int NCB = NB == 3 ? 3 : 2;  // cost buffers
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
-    uint8_t *scs = reinterpret_cast<uint8_t *>(tile + Cx<R>::TILE_ELEMS);
-    V *stab = reinterpret_cast<V *>(scs + 2 * Cx<R>::CS_BYTES);
+    uint8_t *scs = reinterpret_cast<uint8_t *>(tile + (size_t)NB * Cx<R>::TILE_ELEMS);
+    V *stab = reinterpret_cast<V *>(scs + (size_t)NCB * Cx<R>::CS_BYTES);
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) stab[i] = i <= a.m ? tab.t[i] : zero_amp<V>();
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW, FULL>(a, stab, tile, scs);
+    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW, FULL, NB>(a, stab, tile, scs);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -591,8 +617,8 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 // Dynamic shared memory of a pass: the tile buffer, two cost-byte buffers and
 // the phase table (modes that apply a phase).
 template <typename R>
-static size_t pass_smem(bool phase, int m) {
-    return sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS + 2 * (size_t)Cx<R>::CS_BYTES +
+static size_t pass_smem(bool phase, int m, int nb = 1) {
+    return sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS * (size_t)nb + (nb == 3 ? 3 : 2) * (size_t)Cx<R>::CS_BYTES +
            (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
@@ -625,21 +651,22 @@ struct HighSet {
     }
 };
 
-// The kernels of the low pass (Z2: the halved state's mirror variant); all
-// butterfly every tile bit, except init0 (p = 0: the initial state alone).
-template <typename R, bool Z2>
+// The kernels of the low pass (Z2: the halved state's mirror variant; NB:
+// tile buffers per CTA); all butterfly every tile bit, except init0 (p = 0:
+// the initial state alone).
+template <typename R, bool Z2, int NB = 1>
 struct LowSet {
     using Full = PhaseTab<R, MAX_TABLE>;
     using None = PhaseTab<R, 1>;
-    void (*init[2])(PassArgs<R>, Full) = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, Z2, true>,
-                                          pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, Z2, true>};
-    void (*init0)(PassArgs<R>, Full) = pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, Z2, true, HIGH_ROW, false>;
-    void (*phase[2])(PassArgs<R>, Full) = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE, Z2>,
-                                           pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE, Z2>};
-    void (*plain[2])(PassArgs<R>, None) = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, Z2>,
-                                           pass_kernel<R, true, MODE_PLAIN, true, false, 1, Z2>};
-    void (*plain_red[2])(PassArgs<R>, None) = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, Z2, true>,
-                                               pass_kernel<R, true, MODE_PLAIN, true, false, 1, Z2, true>};
+    void (*init[2])(PassArgs<R>, Full) = {pass_kernel<R, true, MODE_INIT, false, false, MAX_TABLE, Z2, true, HIGH_ROW, true, NB>,
+                                          pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, Z2, true, HIGH_ROW, true, NB>};
+    void (*init0)(PassArgs<R>, Full) = pass_kernel<R, true, MODE_INIT, true, false, MAX_TABLE, Z2, true, HIGH_ROW, false, NB>;
+    void (*phase[2])(PassArgs<R>, Full) = {pass_kernel<R, true, MODE_PHASE, false, false, MAX_TABLE, Z2, false, HIGH_ROW, true, NB>,
+                                           pass_kernel<R, true, MODE_PHASE, true, false, MAX_TABLE, Z2, false, HIGH_ROW, true, NB>};
+    void (*plain[2])(PassArgs<R>, None) = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, Z2, false, HIGH_ROW, true, NB>,
+                                           pass_kernel<R, true, MODE_PLAIN, true, false, 1, Z2, false, HIGH_ROW, true, NB>};
+    void (*plain_red[2])(PassArgs<R>, None) = {pass_kernel<R, true, MODE_PLAIN, false, false, 1, Z2, true, HIGH_ROW, true, NB>,
+                                               pass_kernel<R, true, MODE_PLAIN, true, false, 1, Z2, true, HIGH_ROW, true, NB>};
     void all(std::vector<KPtr> &ks) const {
         ks.push_back((KPtr)init0);
         for (int i = 0; i < 2; ++i) {
@@ -666,12 +693,14 @@ struct PassKernels {
     // complex128 has no wide rows and those are the narrow kernels again
     static constexpr int WROW = sizeof(R) == 4 ? HIGH_ROW + 1 : HIGH_ROW;
     LowSet<R, false> low;
+    LowSet<R, false, 3> low3;  // one CTA per SM, three tile buffers (full state, m <= 255)
     typename std::conditional<is_df<R>(), NoLowSet<R>, LowSet<R, true>>::type low_z2;
     HighSet<R, HIGH_ROW, true> high;     // [wide][full] below
     HighSet<R, HIGH_ROW, false> high_part;
     HighSet<R, WROW, true> wide;
     HighSet<R, WROW, false> wide_part;
-    cudaError_t init() {
+    bool low3_ok = false;  // the three-buffer kernels' shared memory fits the device
+    cudaError_t init(size_t smem_optin) {
         const int big = (int)pass_smem<R>(true, MAX_TABLE - 1);
         std::vector<KPtr> ks;
         low.all(ks);
@@ -683,6 +712,16 @@ struct PassKernels {
         for (KPtr k : ks) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
             if (e != cudaSuccess) return e;
+        }
+        const size_t big3 = pass_smem<R>(true, MAX_TABLE - 1, 3);
+        low3_ok = big3 + 1024 <= smem_optin;  // 1 KB for the static reduction buffers
+        if (low3_ok) {
+            std::vector<KPtr> k3;
+            low3.all(k3);
+            for (KPtr k : k3) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big3);
+                if (e != cudaSuccess) return e;
+            }
         }
         return cudaSuccess;
     }
@@ -697,7 +736,9 @@ static int pass_kernels(PassKernels<R> **out) {
     if (dev < 0) return QAOA_ECUDA;
     std::lock_guard<std::mutex> lk(mu);
     if (!state[dev]) {
-        const cudaError_t e = pk.init();
+        DeviceInfo di;
+        if (device_info(&di)) return QAOA_ECUDA;
+        const cudaError_t e = pk.init(di.smem_optin);
         if (e != cudaSuccess) return cuda_error(e, "pass kernel attributes");
         state[dev] = 1;
     }
@@ -786,6 +827,14 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
     typename PassKernels<R>::None none{};
     const std::vector<Launch> seq = make_schedule(pl.n_passes, r.p);
     const dim3 block(Cx<R>::PT), grid(gx, r.batch);
+    // Low passes of one full-state instance take the three-buffer kernels (one
+    // CTA per SM) when they fit the device; their grid is one CTA per SM.
+    DeviceInfo di;
+    if (device_info(&di)) return QAOA_ECUDA;
+    const bool use3 = pk->low3_ok && !z2 && r.batch == 1;
+    const uint64_t tiles_one = 1ull << (pl.state_bits - T);
+    const dim3 grid3((unsigned)(tiles_one < (uint64_t)di.sms ? tiles_one : (uint64_t)di.sms), 1);
+    int last_gx = gx;  // grid width of the pass that writes the p_succ partials
     for (size_t i = 0; i < seq.size(); ++i) {
         const Launch &L = seq[i];
         const Pass &ps = pl.pass[L.pass];
@@ -832,25 +881,32 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         const size_t smem_phase = pass_smem<R>(true, r.m), smem_plain = pass_smem<R>(false, 0);
         if (low) {
             // the full-state or the halved-state set (double-float has only the former)
-            auto launch_low = [&](const auto &ls) -> int {
+            auto launch_low = [&](const auto &ls, dim3 g, size_t sm_phase, size_t sm_plain) -> int {
                 if (L.mode == MODE_INIT) {
                     fill_table<R>(tab, r, 0, sign);
-                    (r.p == 0 ? ls.init0 : ls.init[u1])<<<grid, block, smem_phase, stream>>>(a, *tab);
+                    (r.p == 0 ? ls.init0 : ls.init[u1])<<<g, block, sm_phase, stream>>>(a, *tab);
                 } else if (L.mode == MODE_PHASE) {
                     fill_table<R>(tab, r, L.la, sign);
-                    ls.phase[u1]<<<grid, block, smem_phase, stream>>>(a, *tab);
+                    ls.phase[u1]<<<g, block, sm_phase, stream>>>(a, *tab);
                 } else if (L.mode == MODE_PLAIN) {
-                    (a.reduce ? ls.plain_red[u1] : ls.plain[u1])<<<grid, block, smem_plain, stream>>>(a, none);
+                    (a.reduce ? ls.plain_red[u1] : ls.plain[u1])<<<g, block, sm_plain, stream>>>(a, none);
                 } else {
                     return set_error(QAOA_ECUDA, "schedule: fused low pass");
                 }
+                if (a.reduce) last_gx = (int)g.x;
                 return QAOA_OK;
             };
             int lrc = QAOA_OK;
-            if constexpr (is_df<R>())
-                lrc = z2 ? set_error(QAOA_EINVAL, "double-float takes the full state") : launch_low(pk->low);
-            else
-                lrc = z2 ? launch_low(pk->low_z2) : launch_low(pk->low);
+            if (z2) {
+                if constexpr (is_df<R>())
+                    lrc = set_error(QAOA_EINVAL, "double-float takes the full state");
+                else
+                    lrc = launch_low(pk->low_z2, grid, smem_phase, smem_plain);
+            } else if (use3) {
+                lrc = launch_low(pk->low3, grid3, pass_smem<R>(true, r.m, 3), pass_smem<R>(false, 0, 3));
+            } else {
+                lrc = launch_low(pk->low, grid, smem_phase, smem_plain);
+            }
             if (lrc) return lrc;
         } else {
             // rows of HIGH_ROW or WROW bits; FULL kernels when no bit of the group is a carried one
@@ -881,7 +937,7 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
         rc = profile_after(kind, stream);
         if (rc) return rc;
     }
-    if (want) rc = launch_reduce(d_partials, r.batch, gx, 2, r.d_result, stream);
+    if (want) rc = launch_reduce(d_partials, r.batch, last_gx, 2, r.d_result, stream);
     return rc;
 }
 
