@@ -13,6 +13,7 @@
 //    partials, then a fixed-order reduction (deterministic).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -693,13 +694,19 @@ struct PassKernels {
     // complex128 has no wide rows and those are the narrow kernels again
     static constexpr int WROW = sizeof(R) == 4 ? HIGH_ROW + 1 : HIGH_ROW;
     LowSet<R, false> low;
-    LowSet<R, false, 3> low3;  // one CTA per SM, three tile buffers (full state, m <= 255)
     typename std::conditional<is_df<R>(), NoLowSet<R>, LowSet<R, true>>::type low_z2;
+    // One CTA per SM, three tile buffers: the complex64 low passes of a single
+    // instance (full and halved state).  (Measured in same-box A/Bs: the
+    // strided high passes, the double-float and complex128 low passes and
+    // batched low passes all run slower with one CTA per SM.)
+    static constexpr bool NB3 = std::is_same<R, float>::value;
+    typename std::conditional<NB3, LowSet<R, false, 3>, NoLowSet<R>>::type low3;
+    typename std::conditional<NB3, LowSet<R, true, 3>, NoLowSet<R>>::type low_z2_3;
     HighSet<R, HIGH_ROW, true> high;     // [wide][full] below
     HighSet<R, HIGH_ROW, false> high_part;
     HighSet<R, WROW, true> wide;
     HighSet<R, WROW, false> wide_part;
-    bool low3_ok = false;  // the three-buffer kernels' shared memory fits the device
+    bool nb3_ok = false;  // the three-buffer kernels' shared memory fits the device
     cudaError_t init(size_t smem_optin) {
         const int big = (int)pass_smem<R>(true, MAX_TABLE - 1);
         std::vector<KPtr> ks;
@@ -714,10 +721,11 @@ struct PassKernels {
             if (e != cudaSuccess) return e;
         }
         const size_t big3 = pass_smem<R>(true, MAX_TABLE - 1, 3);
-        low3_ok = big3 + 1024 <= smem_optin;  // 1 KB for the static reduction buffers
-        if (low3_ok) {
+        nb3_ok = big3 + 1024 <= smem_optin;  // 1 KB for the static reduction buffers
+        if (nb3_ok) {
             std::vector<KPtr> k3;
             low3.all(k3);
+            low_z2_3.all(k3);
             for (KPtr k : k3) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big3);
                 if (e != cudaSuccess) return e;
@@ -827,13 +835,15 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
     typename PassKernels<R>::None none{};
     const std::vector<Launch> seq = make_schedule(pl.n_passes, r.p);
     const dim3 block(Cx<R>::PT), grid(gx, r.batch);
-    // Low passes of one full-state instance take the three-buffer kernels (one
-    // CTA per SM) when they fit the device; their grid is one CTA per SM.
+    // The complex64 low passes of a single instance take the three-buffer
+    // kernels (one CTA per SM) when they fit the device: their grid is one CTA
+    // per SM (never wider than gx, the partials buffer's width).
     DeviceInfo di;
     if (device_info(&di)) return QAOA_ECUDA;
-    const bool use3 = pk->low3_ok && !z2 && r.batch == 1;
+    const bool use3 = PassKernels<R>::NB3 && pk->nb3_ok && r.batch == 1;
     const uint64_t tiles_one = 1ull << (pl.state_bits - T);
-    const dim3 grid3((unsigned)(tiles_one < (uint64_t)di.sms ? tiles_one : (uint64_t)di.sms), 1);
+    const int gx3 = std::min(balanced_grid_x(di.sms, r.batch, tiles_one), gx);
+    const dim3 grid3(gx3, r.batch);
     int last_gx = gx;  // grid width of the pass that writes the p_succ partials
     for (size_t i = 0; i < seq.size(); ++i) {
         const Launch &L = seq[i];
@@ -897,13 +907,18 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
                 return QAOA_OK;
             };
             int lrc = QAOA_OK;
-            if (z2) {
+            if constexpr (PassKernels<R>::NB3) {
+                const size_t p3 = pass_smem<R>(true, r.m, 3), q3 = pass_smem<R>(false, 0, 3);
+                if (use3)
+                    lrc = z2 ? launch_low(pk->low_z2_3, grid3, p3, q3) : launch_low(pk->low3, grid3, p3, q3);
+                else
+                    lrc = z2 ? launch_low(pk->low_z2, grid, smem_phase, smem_plain)
+                             : launch_low(pk->low, grid, smem_phase, smem_plain);
+            } else if (z2) {
                 if constexpr (is_df<R>())
                     lrc = set_error(QAOA_EINVAL, "double-float takes the full state");
                 else
                     lrc = launch_low(pk->low_z2, grid, smem_phase, smem_plain);
-            } else if (use3) {
-                lrc = launch_low(pk->low3, grid3, pass_smem<R>(true, r.m, 3), pass_smem<R>(false, 0, 3));
             } else {
                 lrc = launch_low(pk->low, grid, smem_phase, smem_plain);
             }
