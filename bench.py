@@ -268,6 +268,42 @@ def cpu_baseline_sample(p: int, min_seconds: float = 10.0, max_steps: int = 8):
                       f"p={p} (cost table + evolution + p_succ), {dt:.1f} s"}, dt
 
 
+SINGLE_CORE_N = 20
+
+
+def cpu_single_core_sample(p: int, min_seconds: float = 4.0) -> dict | None:
+    """The same oracle step on one host core (a child process with
+    OMP_NUM_THREADS=1, since the thread count is fixed when the library loads),
+    on an n = SINGLE_CORE_N instance, for about `min_seconds`."""
+    code = (
+        "import json, sys, time\n"
+        "sys.path.insert(0, %r)\n"
+        "import oracle\n"
+        "from paper_2401_02852_gb300 import instances as gen\n"
+        "n, p = %d, %d\n"
+        "inst, _ = gen.satisfiable_instance('bench-cpu1', n, %d, %r, 0, oracle.count_solutions)\n"
+        "g, b = gen.linear_ramp(p)\n"
+        "steps, dt = 0, 0.0\n"
+        "while dt < %r:\n"
+        "    t0 = time.perf_counter()\n"
+        "    cost, _, _ = oracle.cost_table(n, inst.var, inst.neg)\n"
+        "    oracle.success_prob(n, cost, oracle.evolve(n, cost, g, b))\n"
+        "    dt += time.perf_counter() - t0\n"
+        "    steps += 1\n"
+        "print(json.dumps({'steps': steps, 'seconds': dt, 'm': inst.m}))\n"
+    ) % (ROOT, SINGLE_CORE_N, p, K_SAT, R_SAT, min_seconds)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        out = json.loads(res.stdout.strip().splitlines()[-1])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
+    n = SINGLE_CORE_N
+    return {"value": (2 ** n) * p * out["steps"] / out["seconds"], "unit": UNIT, "cores": 1,
+            "sample": f"{out['steps']} steps of one NAE-5-SAT instance n={n}, m={out['m']}, p={p}, "
+                      f"{out['seconds']:.1f} s, OMP_NUM_THREADS=1"}
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args, ws, rank):
     """The oracle timed on the host cores (rank 0 only)."""
@@ -316,6 +352,7 @@ def run_native(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _ = cpu_baseline_sample(args.p)
+        cpu["single_core"] = cpu_single_core_sample(args.p)
 
     torch.cuda.set_device(local)
     dist = None
@@ -415,6 +452,21 @@ def run_native(args, ws, rank, local):
     extra = {"p_succ": results["p_succ"], "norm": results["norm"], "n_sol": n_sol, "m": inst.m,
              "passes_per_layer": len(plan), "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kinds.items()},
              "pass_ms_per_step": pass_ms}
+    if "cost_table" in kinds:
+        # The table's work, N m clause tests, against the INT32 lanes of the
+        # device at the clock sampled during the timed steps (128 per SM per
+        # cycle).  The kernel evaluates 32 assignments per 32-bit operation,
+        # counts only the lower half of the table (C(not x) = C(x)) and skips
+        # the clauses that cannot be violated within a block's assignments.
+        ct_ms = kinds["cost_table"][1] / kinds["cost_table"][0]
+        clk_now = clk.summary()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        lanes = sms * 128 * clk_now["sm_mhz"] * 1e6 if clk_now else None
+        extra["cost_table"] = {"ms_per_table": ct_ms, "clause_tests": (2 ** n) * inst.m,
+                               "clause_tests_per_s": (2 ** n) * inst.m / (ct_ms / 1000.0),
+                               "int32_lane_ops_per_s": lanes, "sms": sms,
+                               "sm_mhz": clk_now["sm_mhz"] if clk_now else None,
+                               "table_bytes_per_s": (2 ** n) / (ct_ms / 1000.0)}
     legs = []  # (name, function) run after the headline, each guarded
 
     if rank == 0 and n == N_DEFAULT and p == P_DEFAULT and dtype == "c64" and not args.no_config2:
