@@ -225,6 +225,20 @@ __device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const
     }
 }
 
+// Early landing (complex64 fused high passes): the next tile's elements
+// u < EARLY_ELEMS and all its cost bytes are copied into buffers of their own
+// right after the current tile's first exchange, i.e. about half a tile of
+// compute before the tile buffer frees at the last exchange and takes the
+// rest.  In the load mapping u = tid + (r << LOAD), so those elements are
+// exactly registers r < EARLY_ELEMS >> LOAD (12 of 32), and every thread's
+// copy chunks j < EARLY_ELEMS / (2 PT) (6 of 16): both splits are compile-time.
+// 24 KiB more per CTA (108.5 KiB), still two CTAs per SM.
+constexpr int EARLY_ELEMS = 3072;
+template <typename R, bool LOW, int MODE, int NB>
+__host__ __device__ constexpr bool early_landing() {
+    return !LOW && MODE == MODE_FUSED && NB == 1 && std::is_same<R, float>::value;
+}
+
 // NB = 1: one tile buffer per CTA, two CTAs per SM; the next tile's copies
 // start once the current tile's last exchange is read out.  NB = 3: three tile
 // (and cost) buffers, one CTA per SM; tile i + 2's copies are issued when tile
@@ -232,7 +246,7 @@ __device__ __forceinline__ void issue_tile_z2(const typename Cx<R>::V *st, const
 // cp.async commit-group pipeline: wait_group 2 completes the oldest).
 template <typename R, bool LOW, int MODE, bool UA1, bool UA2, bool Z2, bool RED, int HROW, bool FULL, int NB>
 __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename Cx<R>::V *stab,
-                                           typename Cx<R>::V *tiles_buf, uint8_t *scs) {
+                                           typename Cx<R>::V *tiles_buf, uint8_t *scs, typename Cx<R>::V *ebuf) {
     using G = Cx<R>;
     using V = typename G::V;
     constexpr int T = G::T, NR = G::NR;
@@ -275,6 +289,19 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
     };
     auto tbuf = [&](int b) { return tiles_buf + (size_t)b * G::TILE_ELEMS; };
     auto cbuf = [&](int b) { return scs + (size_t)b * G::CS_BYTES; };
+    constexpr bool EARLY = early_landing<R, LOW, MODE, NB>();
+    constexpr int JE = EARLY_ELEMS / ((16 / (int)sizeof(V)) * G::PT);  // early copy chunks per thread
+    constexpr int RE = EARLY_ELEMS >> LD;                              // early load-mapping registers
+    static_assert(!EARLY || ((RE << LD) == EARLY_ELEMS && JE * (16 / (int)sizeof(V)) * G::PT == EARLY_ELEMS),
+                  "the early part must be whole registers and whole copy chunks");
+    auto issue_early = [&](uint32_t tt, uint8_t *scb) {  // elements below EARLY_ELEMS and the cost bytes
+        if constexpr (EARLY)
+            issue_tile<Cx<R>, true, 0, JE>(st, cs, base_of(tt), row, a.lo, true, true, ebuf, scb);
+    };
+    auto issue_late = [&](uint32_t tt, V *tb) {  // the other elements, into the tile buffer
+        if constexpr (EARLY)
+            issue_tile<Cx<R>, true, JE, -1>(st, cs, base_of(tt), row, a.lo, true, false, tb, nullptr);
+    };
     double acc[2] = {0.0, 0.0};  // p_succ, norm
     const uint32_t tiles = (uint32_t)a.tiles;
     // High passes that read both the state and the cost bytes take tiles in
@@ -290,7 +317,14 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         return grouped ? GT * (blockIdx.x + (i / GT) * gridDim.x) + (i % GT) : blockIdx.x + i * gridDim.x;
     };
     uint32_t t = tile_at(0);
-    if (t < tiles) issue(t, tbuf(0), cbuf(0));
+    if (t < tiles) {
+        if constexpr (EARLY) {
+            issue_early(t, cbuf(0));
+            issue_late(t, tbuf(0));
+        } else {
+            issue(t, tbuf(0), cbuf(0));
+        }
+    }
     cp_async_commit();
     if (NB == 3) {
         const uint32_t t1 = tile_at(1);
@@ -309,7 +343,20 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
         auto prefetch = [&]() {
             if constexpr (NB == 1) {
                 __syncthreads();
-                if (tn < tiles) issue(tn, tbuf(0), cbuf(b ^ 1));
+                if (tn < tiles) {
+                    if constexpr (EARLY)
+                        issue_late(tn, tbuf(0));
+                    else
+                        issue(tn, tbuf(0), cbuf(b ^ 1));
+                }
+                cp_async_commit();
+            }
+        };
+        // EARLY: after the first exchange every thread has read its registers out
+        // of the early buffer, and the other cost buffer held the previous tile's
+        auto early_hook = [&]() {
+            if constexpr (EARLY) {
+                if (tn < tiles) issue_early(tn, cbuf(b ^ 1));
                 cp_async_commit();
             }
         };
@@ -337,10 +384,10 @@ __device__ __forceinline__ void pass_tiles(const PassArgs<R> &a, const typename 
             else if (MODE == MODE_PHASE)
                 v[r] = cmul(tile[u], stab[c]);
             else
-                v[r] = tile[u];
+                v[r] = (EARLY && r < RE) ? ebuf[u] : tile[u];
         }
         if (MODE == MODE_FUSED) {
-            rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, NoHook());
+            rounds_up<G, LOW, UA1>(v, tile, active, a.A1, a.B1, early_hook);
             const uint32_t cb = cost_base<G, LC>(tid);
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = cmul(v[r], stab[sc[cb + G::cidx((uint32_t)r << LC)]]);
@@ -390,12 +437,14 @@ __global__ void __launch_bounds__(Cx<R>::PT, NB == 3 ? 1 : 2) pass_kernel(const 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
     uint8_t *scs = reinterpret_cast<uint8_t *>(tile + (size_t)NB * Cx<R>::TILE_ELEMS);
-    V *stab = reinterpret_cast<V *>(scs + (size_t)NCB * Cx<R>::CS_BYTES);
+    constexpr bool EARLY = early_landing<R, LOW, MODE, NB>();
+    V *ebuf = EARLY ? reinterpret_cast<V *>(scs + (size_t)NCB * Cx<R>::CS_BYTES) : nullptr;
+    V *stab = reinterpret_cast<V *>(scs + (size_t)NCB * Cx<R>::CS_BYTES + (EARLY ? EARLY_ELEMS * sizeof(V) : 0));
     if (MODE != MODE_PLAIN) {  // 256 entries at least: any uint8 cost indexes inside the table
         for (int i = threadIdx.x; i < 256 || i <= a.m; i += Cx<R>::PT) stab[i] = i <= a.m ? tab.t[i] : zero_amp<V>();
         __syncthreads();
     }
-    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW, FULL, NB>(a, stab, tile, scs);
+    pass_tiles<R, LOW, MODE, UA1, UA2, Z2, RED, HROW, FULL, NB>(a, stab, tile, scs, ebuf);
 }
 
 // Fixed-order reduction of per-block partials: out[b][k] = sum_j part[b][j][k].
@@ -618,8 +667,9 @@ int launch_small_batch(int dtype, int n_jobs, const SmallJob *d_jobs, const doub
 // Dynamic shared memory of a pass: the tile buffer, two cost-byte buffers and
 // the phase table (modes that apply a phase).
 template <typename R>
-static size_t pass_smem(bool phase, int m, int nb = 1) {
+static size_t pass_smem(bool phase, int m, int nb = 1, bool early = false) {
     return sizeof(typename Cx<R>::V) * Cx<R>::TILE_ELEMS * (size_t)nb + (nb == 3 ? 3 : 2) * (size_t)Cx<R>::CS_BYTES +
+           (early ? sizeof(typename Cx<R>::V) * EARLY_ELEMS : 0) +
            (phase ? sizeof(typename Cx<R>::V) * table_entries(m) : 0);
 }
 
@@ -708,7 +758,7 @@ struct PassKernels {
     HighSet<R, WROW, false> wide_part;
     bool nb3_ok = false;  // the three-buffer kernels' shared memory fits the device
     cudaError_t init(size_t smem_optin) {
-        const int big = (int)pass_smem<R>(true, MAX_TABLE - 1);
+        const int big = (int)pass_smem<R>(true, MAX_TABLE - 1, 1, std::is_same<R, float>::value);
         std::vector<KPtr> ks;
         low.all(ks);
         low_z2.all(ks);
@@ -938,7 +988,8 @@ static int evolve_passes(const EvolveReq &r, double *d_partials, int gx, cudaStr
                 fill_table<R>(tab, r, L.la + 1, sign);
                 auto k = wide ? (full ? wn.fused[u1][u2] : wp.fused[u1][u2])
                               : (full ? hn.fused[u1][u2] : hp.fused[u1][u2]);
-                k<<<grid, block, smem_phase, stream>>>(a, *tab);
+                const size_t smem_fused = pass_smem<R>(true, r.m, 1, early_landing<R, false, MODE_FUSED, 1>());
+                k<<<grid, block, smem_fused, stream>>>(a, *tab);
             } else if (L.mode == MODE_PLAIN) {
                 auto k = a.reduce ? (wide ? (full ? wn.plain_red[u1] : wp.plain_red[u1])
                                           : (full ? hn.plain_red[u1] : hp.plain_red[u1]))

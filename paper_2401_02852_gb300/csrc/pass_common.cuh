@@ -366,7 +366,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // buf[u] (with PADC the cost byte of u at sc[G::cidx(u)]); thread tid takes
 // chunks tid + PT j, whose addresses are a thread base plus j times a stride.
 // Indices inside one instance fit in 32 bits.
-template <typename G, bool PADC = false>
+// Chunks j in [J0, J1) of each thread only (J1 < 0: all), so that a tile can
+// land in two parts: the chunks of elements below a bound, and the rest.
+template <typename G, bool PADC = false, int J0 = 0, int J1 = -1>
 __device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_t *cs, uint32_t base, int row, int lo,
                                            bool state, bool cost, typename G::V *buf, uint8_t *sc) {
     using V = typename G::V;
@@ -375,6 +377,7 @@ __device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_
     constexpr int NT = G::PT;
     constexpr int NCH = (1 << T) / EPC / NT;             // state chunks per thread
     constexpr int CCH = (1 << T) / 16 / NT;              // cost chunks per thread
+    constexpr int JE = J1 < 0 ? NCH : J1;
     const uint32_t tid = threadIdx.x;
     if (state) {
         // chunk q = tid + PT j covers tile elements [EPC q, EPC q + EPC)
@@ -384,7 +387,7 @@ __device__ __forceinline__ void issue_tile(const typename G::V *st, const uint8_
         const uint32_t step = elem_offset32((uint32_t)(EPC * NT), row, lo);
         char *dst = reinterpret_cast<char *>(buf) + 16 * tid;
 #pragma unroll
-        for (int j = 0; j < NCH; ++j) cp_async16(dst + (size_t)16 * NT * j, st + (off0 + step * j));
+        for (int j = J0; j < JE; ++j) cp_async16(dst + (size_t)16 * NT * j, st + (off0 + step * j));
     }
     if (cost) {
         const uint32_t off0 = base + elem_offset32(16u * tid, row, lo);
