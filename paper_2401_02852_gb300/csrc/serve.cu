@@ -2,7 +2,9 @@
 // paper; a serving pattern around its simulation).
 //
 // One scheduler thread per server.  Requests are copied at submit time and
-// queued.  Each scheduler iteration (1) retires finished work by querying CUDA
+// queued.  Finished work is retired by the host callback enqueued behind it
+// (or, if the scheduler sees the completion event first, by the scheduler).
+// Each scheduler iteration (1) retires finished work it finds by querying CUDA
 // events, (2) admits waiting requests in arrival order while a slot (a CUDA
 // stream with its own staging) is free and the device-memory footprint fits
 // the budget:
@@ -20,9 +22,10 @@
 //     behind it are still packed into free slots (their footprint is a table).
 // Device memory for tables and states comes from cudaMallocAsync on the slot's
 // stream and returns with cudaFreeAsync, so admission never synchronises the
-// device.  Results land in pinned host memory and are published when the
-// slot's completion event fires; a host callback enqueued behind the event
-// wakes the scheduler, which otherwise sleeps (bounded waits only).
+// device.  Results land in pinned host memory; the host callback enqueued
+// behind the slot's completion event publishes them (no CUDA call in it) and
+// wakes the waiters and the scheduler, which otherwise sleeps (bounded waits
+// only).
 #include <cuda_runtime.h>
 #include <time.h>
 
@@ -76,6 +79,7 @@ struct Slot {
     void *d_cost = nullptr, *d_state = nullptr;  // large job buffers (freed async)
     int kind = 0;                            // SLOT_SINGLE, SLOT_PACKED or SLOT_GROUP
     size_t res_off = 0;                      // packed / group: offset of the stats block in staging
+    uint64_t gen = 0;                        // launches on this slot so far
 };
 
 }  // namespace qaoa
@@ -117,21 +121,43 @@ static int ensure_stage(Slot &s, size_t bytes) {
     return QAOA_OK;
 }
 
-// Enqueued on a slot's stream behind its completion event: wakes the scheduler
-// (which then finds the event complete).  Runs on a CUDA callback thread and
-// calls no CUDA function; server destruction synchronises every stream first.
+static void retire(qaoa_server *sv, Slot &s);
+
+// The callback's argument: which launch on which slot it follows.
+struct DoneToken {
+    qaoa_server *sv;
+    Slot *slot;
+    uint64_t gen;
+};
+
+// Enqueued on a slot's stream behind its completion event, so the slot's
+// results are in pinned host memory when it runs: it publishes them (unless
+// the scheduler already has, or the slot has moved on to later work) and
+// wakes the waiters and the scheduler.  Runs on a CUDA callback thread and
+// calls no CUDA function; no thread holds the server's lock across a CUDA call
+// that could wait for it, and server destruction synchronises every stream
+// before freeing the server.
 static void CUDART_CB slot_done_callback(void *arg) {
-    qaoa_server *sv = static_cast<qaoa_server *>(arg);
+    DoneToken *tk = static_cast<DoneToken *>(arg);
+    qaoa_server *sv = tk->sv;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
+        if (tk->slot->busy && tk->slot->gen == tk->gen) retire(sv, *tk->slot);
         sv->epoch++;
     }
+    delete tk;
+    sv->cv_done.notify_all();
     sv->cv_work.notify_all();
 }
 
 static int finish_slot(qaoa_server *sv, Slot &s) {
     QAOA_CUDA_TRY(cudaEventRecord(s.done, s.stream));
-    QAOA_CUDA_TRY(cudaLaunchHostFunc(s.stream, slot_done_callback, sv));
+    DoneToken *tk = new DoneToken{sv, &s, s.gen};
+    const cudaError_t e = cudaLaunchHostFunc(s.stream, slot_done_callback, tk);
+    if (e != cudaSuccess) {
+        delete tk;
+        return cuda_error(e, "cudaLaunchHostFunc");
+    }
     return QAOA_OK;
 }
 
@@ -492,6 +518,7 @@ static void scheduler(qaoa_server *sv) {
                 kind = batch.size() > 1 ? SLOT_GROUP : SLOT_SINGLE;
             }
             s.busy = true;
+            s.gen++;
             s.bytes = bytes;
             s.reqs = batch;
             s.t_start = now_ns();
