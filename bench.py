@@ -540,6 +540,9 @@ def run_native(args, ws, rank, local):
                                                                  fd_instances=1, reference=load_golden("grad_n22_p20_oracle.json"))))
         if not args.no_sweep:
             legs.append(("sweep", lambda: workloads.sweep_workload(ns=range(16, 33, 2), seeds=args.seeds)))
+        if not args.no_batch:
+            legs.append(("config1_batch", lambda: workloads.batch_workload(
+                reference=load_golden("batch_n12_p5_oracle.json"))))
         if args.serve_requests > 0:
             legs.append(("serving", lambda: workloads.serve_workload(count=args.serve_requests, rate_hz=200.0)))
         if not args.no_rate_sweep:
@@ -601,7 +604,7 @@ def run_workload(args):
                                           ps=tuple(int(p) for p in args.ps.split(",")),
                                           count=args.count, lr=args.lr)
     else:
-        res = workloads.batch_workload()
+        res = workloads.batch_workload(reference=load_golden("batch_n12_p5_oracle.json"))
     res["workload"] = args.workload
     res["wall_seconds"] = time.perf_counter() - t0
     print(json.dumps(res), flush=True)
@@ -628,6 +631,7 @@ def main():
     ap.add_argument("--no-config2", action="store_true", help="skip the five n=30 instances against the oracle")
     ap.add_argument("--no-grad", action="store_true", help="skip the batched-gradient workload")
     ap.add_argument("--no-sweep", action="store_true", help="skip the scaling sweep")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 100 x n=12 complex128 batch")
     ap.add_argument("--quick", action="store_true", help="headline only (no extra workloads)")
     ap.add_argument("--workload", choices=["evolve", "serve", "grad", "sweep", "batch", "sample", "protocol"], default="evolve")
     ap.add_argument("--requests", type=int, default=20000)
@@ -646,7 +650,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-2, help="protocol: Adam learning rate of the angle training")
     args = ap.parse_args()
     if args.quick:
-        args.no_config2 = args.no_grad = args.no_sweep = args.no_rate_sweep = True
+        args.no_config2 = args.no_grad = args.no_sweep = args.no_rate_sweep = args.no_batch = True
         args.z2 = args.compare_c128 = False
         args.serve_requests = 0
     ws, rank, local = dist_env()

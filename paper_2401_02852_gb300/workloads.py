@@ -234,7 +234,13 @@ def sweep_workload(ns=range(16, 33, 2), ps=(1, 4, 10, 20), seeds: int = 200, out
     return out
 
 
-def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p: int = 5, reps: int = 20) -> dict:
+def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p: int = 5, reps: int = 20,
+                   reference: Optional[dict] = None) -> dict:
+    """One launch evolving ``count`` small instances (complex128, FP64 and
+    double-float).  ``reference`` (optional) holds stored FP64 results of the
+    same instances ({"instances": [{"index", "attempt", "n_sol", "cost_sha256",
+    "p_succ"}, ...]}): the cost tables are compared byte for byte (by hash) and
+    p_succ relatively."""
     insts = [gen.satisfiable_instance("batch-cfg", n, k, r, i, lambda x: api.cost_table(x)[1])[0]
              for i in range(count)]
     costs, sols, _ = api.cost_table_batch(insts)
@@ -263,6 +269,26 @@ def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p:
     _sync()
     dtdf = (time.perf_counter() - t0) / reps
     sol = sols > 0
+    vs_ref = None
+    if reference is not None:
+        import hashlib
+
+        recs = {rec["index"]: rec for rec in reference["instances"]}
+        tables = costs.cpu().numpy()
+        same_inst = same_table = 0
+        rel, rel_df = [], []
+        for i, inst in enumerate(insts):
+            rec = recs.get(i)
+            if rec is None or rec["attempt"] != inst.seed_key[-1]:
+                continue
+            same_inst += 1
+            h = hashlib.sha256(np.ascontiguousarray(tables[i]).tobytes()).hexdigest()
+            same_table += int(h == rec["cost_sha256"] and int(sols[i]) == rec["n_sol"])
+            rel.append(abs(ps[i] - rec["p_succ"]) / rec["p_succ"])
+            rel_df.append(abs(psdf[i] - rec["p_succ"]) / rec["p_succ"])
+        vs_ref = {"instances": same_inst, "cost_tables_bit_exact": same_table,
+                  "max_c128_rel_err": float(max(rel)) if rel else None,
+                  "max_df64_rel_err": float(max(rel_df)) if rel_df else None}
     return {"count": count, "n": n, "m": insts[0].m, "p": p, "ms_per_batch": dt * 1e3,
             "amp_layer_per_s": count * (1 << n) * p / dt,
             "roofline": {"bound": "fp64", "achieved_tflops": flops / dt / 1e12, "peak_tflops": fp64_nominal / 1e12,
@@ -271,7 +297,8 @@ def batch_workload(count: int = 100, n: int = 12, k: int = 3, r: float = 2.0, p:
             "max_norm_err": float(np.max(np.abs(nm - 1))), "mean_nsol": float(np.mean(sols)),
             "df64": {"ms_per_batch": dtdf * 1e3, "speedup_over_fp64": dt / dtdf,
                      "max_psucc_rel_diff_vs_fp64": float(np.max(np.abs(psdf[sol] - ps[sol]) / ps[sol])),
-                     "max_amp_diff_vs_fp64": float((stdf - states).abs().max())}}
+                     "max_amp_diff_vs_fp64": float((stdf - states).abs().max())},
+            "vs_oracle": vs_ref}
 
 
 def protocol_workload(ks=(9,), ps=(1, 2, 4, 8, 16, 32), count: int = 2500, lr: float = 1e-2) -> dict:

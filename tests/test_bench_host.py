@@ -41,3 +41,7 @@ def test_stored_oracle_results_load():
     grad = bench.load_golden("grad_n22_p20_oracle.json")
     assert grad["n"] == 22 and len(grad["instances"][0]["dgamma"]) == 20
     assert bench.load_golden("missing.json") is None
+    batch = bench.load_golden("batch_n12_p5_oracle.json")
+    assert batch["n"] == 12 and batch["p"] == 5 and len(batch["instances"]) == 100
+    assert all(r["n_sol"] > 0 and len(r["cost_sha256"]) == 64 and abs(r["norm"] - 1) < 1e-12
+               for r in batch["instances"])
