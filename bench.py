@@ -471,11 +471,13 @@ def run_native(args, ws, rank, local):
                                "table_bytes_per_s": (2 ** n) / (ct_ms / 1000.0)}
     legs = []  # (name, function) run after the headline, each guarded
 
-    if rank == 0 and n == N_DEFAULT and p == P_DEFAULT and dtype == "c64" and not args.no_config2:
+    # The extra workloads run in a single-process run only; with several ranks
+    # the line carries the replicated headline alone.
+    if ws == 1 and n == N_DEFAULT and p == P_DEFAULT and dtype == "c64" and not args.no_config2:
         def config2():
             return config2_seeds(n, p, g, b)
         legs.append(("config2_five_seeds", config2))
-    if args.z2 and rank == 0:
+    if args.z2 and ws == 1:
         def z2_leg():
             # the halved state (exact by the global-flip symmetry): same p_succ, half the bytes
             from paper_2401_02852_gb300._lib import Z2_HALF
@@ -501,7 +503,7 @@ def run_native(args, ws, rank, local):
                     "p_succ": hres["p"], "p_succ_rel_diff_vs_full": abs(hres["p"] - results["p_succ"]) /
                     results["p_succ"], "stored_state_GB": (2 ** (n - 1)) * es / 1e9}
         legs.append(("z2_halved", z2_leg))
-    if args.compare_c128 and dtype == "c64" and rank == 0:
+    if args.compare_c128 and dtype == "c64" and ws == 1:
         def c128_leg():
             st128 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
             api.evolve(n, cost, inst.m, g, b, "c128", out=st128)
@@ -535,7 +537,7 @@ def run_native(args, ws, rank, local):
             del st128, std
             return out
         legs.append(("c128_compare", c128_leg))
-    if rank == 0 and ws == 1:
+    if ws == 1:
         from paper_2401_02852_gb300 import workloads
         if not args.no_grad:
             legs.append(("grad", lambda: workloads.grad_workload(batch=256, n=22, p=20, adam_steps=args.adam_steps,
