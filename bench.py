@@ -310,6 +310,10 @@ def run_reference(args, ws, rank):
     """The oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
         return 0
+    if ws > 1 and os.environ.get("OMP_NUM_THREADS") == "1":
+        # torchrun sets one OpenMP thread per process; the oracle's only process
+        # takes the host's cores (read when the oracle's OpenMP runtime loads)
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     import oracle
     from paper_2401_02852_gb300 import instances as gen
 
@@ -355,11 +359,21 @@ def run_native(args, ws, rank, local):
         cpu, _ = cpu_baseline_sample(args.p)
         cpu["single_core"] = cpu_single_core_sample(args.p)
 
+    # one GPU per rank; ranks beyond the visible GPUs (a gloo check of the
+    # multi-rank path) share them
+    local = local % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # nccl (one GPU per rank); QAOA_DIST_BACKEND=gloo lets several ranks
+        # share one GPU, to exercise the multi-rank path where only one GPU is
+        # at hand (only host barriers and scalar reductions cross ranks)
+        backend = os.environ.get("QAOA_DIST_BACKEND", "nccl")
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     n, p = args.n, args.p
     dtype = args.dtype
     es = 8 if dtype == "c64" else 16
@@ -400,7 +414,7 @@ def run_native(args, ws, rank, local):
     launches = api.launch_count() - launches0
     ms = e0.elapsed_time(e1)
     from paper_2401_02852_gb300 import dist as qdist  # replicas: only scalars cross ranks
-    dev = "cuda" if dist is not None else "cpu"
+    dev = "cuda" if dist is not None and dist.get_backend() == "nccl" else "cpu"
     ms_max = 1000.0 * qdist.max_over_ranks(ms / 1000.0, device=dev)
     value = qdist.job_throughput(float((2 ** n) * p * args.steps), ms / 1000.0, device=dev)
 
