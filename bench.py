@@ -461,7 +461,8 @@ def run_native(args, ws, rank, local):
             api.psucc_host(inst, g, b, dtype, work=work)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": (2 ** n) * p * args.steps / dt * ws, "unit": UNIT,
+        # the units of every rank over the slowest rank's time, as for the headline
+        e2e = {"value": qdist.job_throughput(float((2 ** n) * p * args.steps), dt, device=dev), "unit": UNIT,
                "h2d_bytes_per_step": int(inst.var.nbytes + inst.neg.nbytes + 2 * 8 * p),
                "d2h_bytes_per_step": 16}
 
